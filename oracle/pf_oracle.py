@@ -99,14 +99,13 @@ def initial_phi(p):
     """phi0 = [1 + tanh(s / (2 eps))] / 2 with s the signed distance, phi = 1 in
     the drop (Section 2, footnote on the equilibrium profile).
 
-    The drop is centred in the box. Its radius is R(theta) = R (1 + a cos(n
+    The drop is centred in the box (at n_d h / 2 along each axis). Its radius is R(theta) = R (1 + a cos(n
     theta)) in 2D and R (1 + a P_n(cos theta)) in 3D (theta measured from the z
     axis); R(theta) - r is taken as the signed distance for a perturbed drop.
     """
     g = Grid(p["dim"], p["n"], p["L"])
     X = g.centres()
-    c = 0.5 * g.L
-    rel = [x - c for x in X]
+    rel = [X[d] - 0.5 * g.n[d] * g.h for d in range(g.dim)]
     r = np.sqrt(sum(v * v for v in rel))
     R = p["R"]
     m, a = int(p.get("pert_mode", 0)), float(p.get("pert_amp", 0.0))

@@ -1,0 +1,339 @@
+"""Throughput of the fractional step (pf_step) on one GB300, in Mcell-steps/s.
+
+Default workload: the 384^3 mode-2 oscillating drop (density and viscosity
+ratio 10, CDI + energy-based force, mixed precision: float32 stencils and
+V-cycles inside float64 CG). One timed step is one pf_step call: four RK
+stages, each with its phase-field/momentum stage kernels and one variable-
+coefficient Poisson solve. The state (~1.4 GB) is far larger than L2, so no
+flush is needed between steps.
+
+The JSON line also carries: the roofline of the dominant kernel class (timed
+live with CUDA events inside the library's tracing hooks), an end-to-end
+number through the C ABI with the state copied from and to pinned host memory
+every step, the FP64 oracle timed on the host cores on a bounded sample, the
+SM clocks sampled during the timed region and the number of kernel launches.
+
+`--impl reference` times the FP64 oracle (the only reference there is: the
+paper has no code) on the host on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one per rank (the single-grid step
+is not sharded); value = cells x steps of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pf_inputs as I  # noqa: E402
+
+METRIC = "Mcell-steps/s per pf_step"
+UNIT = "Mcell-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+def workload(name, n=None):
+    if name == "osc384":
+        p = I.oscillating_drop_384(precision="mixed", n=n or 384)
+        desc = (f"3D mode-2 oscillating drop {p['n'][0]}^3 periodic, R=0.25, a=0.05R, "
+                "rho ratio 10, mu ratio 10, CDI + EB, mixed precision")
+    elif name == "osc384_fp64":
+        p = I.oscillating_drop_384(precision="fp64", n=n or 384)
+        desc = f"same drop {p['n'][0]}^3, plain FP64"
+    elif name == "drop256":
+        p = I.static_drop_256_r1000(precision="mixed")
+        desc = "2D static drop 256^2, rho ratio 1000, mu ratio 100, CDI + EB, mixed"
+    elif name == "drop64":
+        p = I.static_drop_64()
+        desc = "2D static drop 64^2, FP64, CDI + EB, La = 12000"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return p, desc
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d and isinstance(d[k], (int, float)):
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# Algorithmic bytes per cell and launch of each kernel class (float32 fields,
+# float64 CG vectors; see the design doc for the derivation).
+def algo_bytes_per_cell(cls, dim, w):
+    d = dim
+    table = {
+        # red or black half sweep on the finest level: read x, f, phi, write half of x
+        "mg_gs_level0": 3 * w + 0.5 * w,
+        # p = z + beta p, q = A p, p.q: read z, p, phi; write p, q
+        "cg_dir_spmv": w + 8 + w + 8 + 8,
+        # x += a p, r -= a q, r.r: read p, q, x, r; write x, r, r32
+        "cg_update": 4 * 8 + 2 * 8 + (w if w == 4 else 0),
+        # r.z, z.q: read z, r, q
+        "cg_dots": w + 16,
+        # stage kernel: read phi_s, u_s, phi_n, u_n, normals, aux, acc; write phi, u*, acc
+        "stage": (1 + d + 1 + d + d + 1 + (1 + d)) * w + (1 + d + 1 + d) * w,
+        "cell_pass": w + (d + 1) * w,
+        "correct": (1 + d) * w + 8 + d * w,
+        "divergence": d * w + 8,
+        "mg_restrict": 3 * w + w / (2 ** d),
+        "mg_prolong": 2 * w + w / (2 ** d),
+    }
+    return table.get(cls)
+
+
+def cpu_sample_rate(p, steps=2, n=32):
+    """The oracle (as it stands) on a bounded sample: `steps` RK4 steps of the same
+    drop at n^d cells. Returns (Mcell-steps/s, cores, description)."""
+    from oracle import pf_oracle as O
+
+    q = dict(p)
+    q["n"] = (n, n, n if p["dim"] == 3 else 1)
+    q["eps"] = None
+    q["dt"] = None
+    q["precision"] = "fp64"
+    q = I.finalize(q)
+    po = O.params_from(q)
+    st = O.initial_state(po)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = O.step(st, po)
+    dt = time.perf_counter() - t0
+    cells = n ** p["dim"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    desc = (f"{steps} RK4 steps of the same drop at {n}^{p['dim']} (float64 numpy oracle with "
+            f"a sparse direct pressure solve; the full {p['n'][0]}^{p['dim']} grid is out of "
+            f"reach of the oracle)")
+    return cells * steps / dt / 1e6, cores, desc
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p, desc = workload(args.workload, args.n)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_sample_rate(p, steps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, sdesc = cpu_sample_rate(p, steps=1)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": wall / max(args.steps, 1) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "sample": sdesc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sdesc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2205_05835_gb300 as pf
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    p, desc = workload(args.workload, args.n)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = pf.Simulation(p, stream=stream)
+    ncell = sim.ncell
+    for _ in range(args.warmup):
+        sim.step(1)
+    diag0 = sim.diagnostics()
+    pf.pf_profile_read(sim.ctx, reset=True)
+    pf.pf_profile_enable(sim.ctx, True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = pf.pf_profile_read(sim.ctx, reset=True)
+    pf.pf_profile_enable(sim.ctx, False)
+    diag = sim.diagnostics()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ncell * world * args.steps / (ms / 1e3) / 1e6
+    launches = int(sum(v[0] for v in prof.values()))
+
+    # dominant kernel class and its roofline
+    w = 4 if p["precision"] == "mixed" else 8
+    ranked = sorted(((v[1], k, v[0]) for k, v in prof.items() if v[0] > 0), reverse=True)
+    dom_ms, dom, dom_n = ranked[0]
+    peak, peak_kind = measured_hbm()
+    bpc = algo_bytes_per_cell(dom, p["dim"], w)
+    roof = None
+    if bpc is not None and dom_n > 0:
+        avg_s = dom_ms / dom_n / 1e3
+        achieved = bpc * ncell / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "algo_bytes_per_launch": bpc * ncell,
+                "avg_launch_us": avg_s * 1e6,
+                "share_of_step": dom_ms / ms if ms > 0 else None}
+
+    # end to end through the C ABI: state from / to pinned host memory every step
+    e2e = None
+    if not args.no_e2e:
+        nb = sim.state_bytes()
+        h_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        h_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        pf.pf_get_state(sim.ctx, h_in.data_ptr())
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pf.pf_set_state(sim.ctx, h_in.data_ptr())
+            sim.step(1)
+            pf.pf_get_state(sim.ctx, h_out.data_ptr())
+        barrier()
+        et = time.perf_counter() - t0
+        e2e = {"value": ncell * world * e2e_steps / et / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sdesc = cpu_sample_rate(p, steps=2)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if p["precision"] == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": desc, "cells": ncell, "dt": p["dt"],
+                       "poisson_rtol": p["poisson_rtol"],
+                       "l2": "state > L2 (no flush needed)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": launches,
+            "poisson_iters_last": diag["poisson_iters"],
+            "poisson_iters_max": diag["poisson_iters_max"],
+            "poisson_relres_last": diag["poisson_relres"],
+            "kernel_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0] > 0},
+            "kernel_launches": {k: v[0] for k, v in prof.items() if v[0] > 0},
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="osc384")
+    ap.add_argument("--n", type=int, default=None, help="override the grid size (testing)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

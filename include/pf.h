@@ -1,0 +1,194 @@
+/*
+ * pf.h -- C ABI of the GB300 phase-field two-phase flow step.
+ *
+ * One library call advances a one-fluid, variable-density, incompressible
+ * two-phase flow on a uniform periodic staggered grid by one fractional time
+ * step. The interface is captured by a second-order conservative phase field
+ * phi in [0, 1] (phi = 1 inside the drop) evolved by one of the three models
+ * of Table 1 of Mirjalili, Khanwale & Mani (arXiv 2205.05835):
+ *   CDI   g = Gamma div[eps grad phi - phi (1 - phi) n]            (Table 1)
+ *   SB    g = Gamma [eps lap phi - psi'/eps + eps |grad phi| kappa] (Table 1)
+ *   ISODI g = Gamma [eps lap phi - psi'/eps + phi (1 - phi) kappa]  (Table 1)
+ * Surface tension enters the momentum equation as one of
+ *   EB    F = mu grad phi, mu = (6 sigma/eps) psi' - 6 sigma eps lap phi
+ *         (Eq. eb_st with Eq. ac_mu and sigma_hat = 6 sigma, Section 2)
+ *   CSF   F = sigma kappa grad phi                                  (Section 2)
+ *   LCSF  F = 6 sigma kappa phi (1 - phi) grad phi                  (Eq. equivalence)
+ * and the velocity is projected onto divergence-free fields by solving the
+ * variable-coefficient Poisson equation div(grad p / rho) = div(u*) / tau
+ * with a multigrid-preconditioned conjugate-gradient method.
+ * The time integrator is projected RK4 (Section 3) or forward Euler.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a pf_status; PF_OK is 0. Errors found on the GPU
+ *    (non-convergence, non-finite values) are latched in a device status word
+ *    and returned by the next call that synchronises (pf_step, pf_project,
+ *    pf_diagnostics, pf_get_field, pf_sync).
+ *  - Arrays are structure-of-arrays with x the fastest index:
+ *    idx = (k * ny + j) * nx + i. Velocity component d lives on the d-faces;
+ *    face i - 1/2 along d is stored at the index of cell i. Field arrays passed
+ *    across the ABI are float64 with nx*ny*nz entries, in host or device
+ *    memory (the library uses unified addressing to tell them apart).
+ *  - Memory ownership: the caller allocates the device workspace (size from
+ *    pf_workspace_size) and keeps it alive until pf_destroy; the library never
+ *    allocates or frees device memory itself and never frees caller memory.
+ *    The pf_ctx object is host memory owned by the library (freed by
+ *    pf_destroy). A small pinned host buffer is allocated per context.
+ *  - Streams: all GPU work of a context is issued on the stream given to
+ *    pf_init (a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream). Calls on one context are not thread safe.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PF_OK = 0,
+    PF_ERR_INVALID = 1,        /* bad parameter, size or pointer */
+    PF_ERR_CUDA = 2,           /* a CUDA runtime call failed; see pf_last_error */
+    PF_ERR_NOT_CONVERGED = 3,  /* Poisson solve hit poisson_maxit before poisson_rtol */
+    PF_ERR_NONFINITE = 4,      /* NaN or Inf found in the state */
+    PF_ERR_UNBOUNDED = 5,      /* phi left [-bound_tol, 1 + bound_tol] (when checked) */
+    PF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+    PF_ERR_WORKSPACE = 7       /* workspace pointer misaligned or too small */
+} pf_status;
+
+enum { PF_CDI = 0, PF_SB = 1, PF_ISODI = 2 };               /* phase-field model (Table 1) */
+enum { PF_FORCE_EB = 0, PF_FORCE_CSF = 1, PF_FORCE_LCSF = 2 }; /* surface tension force */
+enum { PF_FP64 = 0, PF_MIXED = 1 };                         /* precision of stencils and V-cycles */
+enum { PF_RK4_PROJ = 0, PF_FE = 1 };                        /* time integrator */
+enum { PF_FIELD_PHI = 0, PF_FIELD_U = 1, PF_FIELD_V = 2, PF_FIELD_W = 3, PF_FIELD_P = 4 };
+
+typedef struct {
+    int dim;              /* 2 or 3 */
+    int n[3];             /* cells per axis (n[2] = 1 in 2D); each >= 4; the box is n[d]*L/n[0] long */
+    double L;             /* box length along x; dx = L / n[0] (uniform spacing) */
+    int model;            /* PF_CDI, PF_SB or PF_ISODI */
+    int force;            /* PF_FORCE_EB, PF_FORCE_CSF or PF_FORCE_LCSF */
+    int precision;        /* PF_FP64: everything in float64.
+                             PF_MIXED: phi, u and the stencils in float32, the double-well
+                             psi'(phi) in float64, the Poisson solve as float64 CG with a
+                             float32 multigrid preconditioner, reductions in float64 */
+    int scheme;           /* PF_RK4_PROJ or PF_FE */
+    double sigma;         /* surface tension coefficient */
+    double eps;           /* interface thickness parameter epsilon */
+    double rho_in, rho_out;  /* densities for phi = 1 and phi = 0; rho linear in clip(phi,0,1) */
+    double mu_in, mu_out;    /* dynamic viscosities, linear in clip(phi,0,1) */
+    double gamma_fixed;   /* > 0: Gamma fixed; else Gamma = max(gamma_min, max|u^n|) per step */
+    double gamma_min;
+    double dt;            /* time step */
+    double delta_n;       /* regulariser of the normal grad phi / (|grad phi| + delta_n) */
+    double poisson_rtol;  /* stop when ||r|| <= rtol * ||rhs|| (float64 residual) */
+    int poisson_maxit;    /* iteration cap of each Poisson solve */
+    double R;             /* initial drop radius (box centre) */
+    int pert_mode;        /* surface perturbation mode n (0: none) */
+    double pert_amp;      /* relative amplitude a: R(theta) = R (1 + a cos n theta) [2D],
+                             R (1 + a P_n(cos theta)) [3D] */
+    int mg_pre, mg_post;  /* red-black Gauss-Seidel sweeps before/after coarse correction (0: 1) */
+    double bound_tol;     /* > 0: flag PF_ERR_UNBOUNDED when phi leaves [-tol, 1 + tol] */
+    int reserved[8];      /* must be zero */
+} pf_params;
+
+typedef struct {
+    double mass;          /* sum phi dV */
+    double ke;            /* 1/2 sum_faces rho_f u_d^2 dV */
+    double se;            /* sum [(6 sigma/eps) psi + 3 sigma eps |grad phi|^2] dV */
+    double umax;          /* max |u_d| over all faces */
+    double ca_inf;        /* umax * mu_in / sigma (Section 3.1) */
+    double dp_laplace;    /* mean(p | phi >= 0.999) - mean(p | phi <= 0.001) */
+    double phi_min, phi_max;
+    double poisson_relres;/* relative residual of the last Poisson solve */
+    double gamma;         /* Gamma used by the last step */
+    int poisson_iters;    /* CG iterations of the last Poisson solve */
+    int poisson_iters_max;/* largest iteration count since the last pf_diagnostics */
+    long long step;
+    double t;
+} pf_diag;
+
+typedef struct pf_ctx pf_ctx;
+
+/* Bytes of device workspace a context with these parameters needs (256-byte
+ * aligned base required). Returns PF_ERR_INVALID for unsupported parameters. */
+pf_status pf_workspace_size(const pf_params* prm, size_t* bytes);
+
+/* Create a context on the current CUDA device. workspace: device memory of at
+ * least pf_workspace_size bytes, 256-byte aligned, owned by the caller.
+ * phi0: optional float64 initial phase field (host or device, nx*ny*nz);
+ * NULL computes phi0 = [1 + tanh((R(theta) - r) / (2 eps))] / 2 on the GPU
+ * (equilibrium profile, footnote to Eq. ac_mu). Velocity and pressure start at 0.
+ * stream: cudaStream_t as void* (NULL: default stream). */
+pf_status pf_init(const pf_params* prm, void* workspace, size_t workspace_bytes,
+                  const double* phi0, void* stream, pf_ctx** out);
+
+/* Advance nsteps time steps (Gamma from max|u^n| at each step start unless
+ * fixed). Synchronises at the end and returns the latched device status. */
+pf_status pf_step(pf_ctx* ctx, int nsteps);
+
+/* Project the current velocity onto divergence-free fields with rho(phi) and
+ * tau = dt; stores the resulting pressure. */
+pf_status pf_project(pf_ctx* ctx);
+
+/* Reductions over the current state (Section 3.1 Ca_inf, Section 3.2 energies);
+ * synchronises the stream. */
+pf_status pf_diagnostics(pf_ctx* ctx, pf_diag* out);
+
+/* Copy one field out as float64 (PF_FIELD_*; pressure returned with zero mean).
+ * dst: host or device memory of nx*ny*nz doubles. Synchronises. */
+pf_status pf_get_field(pf_ctx* ctx, int field, double* dst);
+
+/* Overwrite one field from float64 host or device memory (rounded to the
+ * storage precision). */
+pf_status pf_set_field(pf_ctx* ctx, int field, const double* src);
+
+/* Raw state (phi, u, p, step, t) in storage precision, for checkpoint/restart
+ * and host round trips: pf_state_bytes gives the size; dst/src host or device. */
+size_t pf_state_bytes(const pf_ctx* ctx);
+pf_status pf_get_state(pf_ctx* ctx, void* dst);
+pf_status pf_set_state(pf_ctx* ctx, const void* src);
+
+/* Operator-level entry points (used by parity tests).
+ * pf_eval_rhs: the phase-field right-hand side (Eq. 1 with Table 1) and the
+ * momentum right-hand side without pressure (viscous + advective + F/rho_f) at
+ * the current state for a given Gamma; outputs are float64 arrays (host or
+ * device) of nx*ny*nz (kphi) and dim*nx*ny*nz (ku, components back to back). */
+pf_status pf_eval_rhs(pf_ctx* ctx, double gamma, double* kphi, double* ku);
+
+/* pf_poisson_solve: solve -div(grad x / rho(phi)) = rhs for the current phi
+ * (rhs projected to zero mean; x returned with zero mean). rhs, x: float64,
+ * host or device. x is also the initial guess. Reports iterations and the
+ * final relative residual. */
+pf_status pf_poisson_solve(pf_ctx* ctx, const double* rhs, double* x,
+                           int* iters, double* relres);
+
+/* Tracing: per kernel class, the number of launches and (when timing is
+ * enabled) the summed CUDA-event duration on the context's stream. Launch
+ * counts are always kept; timing records an event pair around each launch
+ * and is off by default. pf_profile_read fills up to max_entries entries
+ * (names are static strings), returns the number of classes, synchronises the
+ * stream, and clears the counters when reset != 0. */
+typedef struct {
+    const char* name;
+    long long launches;
+    double ms;
+} pf_profile_entry;
+pf_status pf_profile_enable(pf_ctx* ctx, int enable);
+int pf_profile_read(pf_ctx* ctx, pf_profile_entry* out, int max_entries, int reset);
+
+/* Wait for all work of the context and return the latched device status. */
+pf_status pf_sync(pf_ctx* ctx);
+
+void pf_destroy(pf_ctx* ctx);
+
+/* Text of the last error of a context (or of the last failed pf_init when
+ * ctx is NULL). Valid until the next call on the context. */
+const char* pf_last_error(const pf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

@@ -1,0 +1,830 @@
+// C ABI (include/pf.h) and the host-side orchestration of one fractional step:
+// workspace layout, projected RK4 / forward Euler stage sequence, the
+// multigrid-preconditioned CG loop, diagnostics and state transfer.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/pf.h"
+#include "pf_internal.h"
+
+using namespace pf;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+// Sequential carving of the caller's workspace (also used with base == nullptr
+// to compute the size).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off = align_up(off + count * sizeof(T));
+        return p;
+    }
+};
+
+const char* kClassNames[KC_COUNT] = {
+    "cell_pass", "stage", "gamma", "divergence", "correct", "mg_coarsen_beta", "mg_gs_level0",
+    "mg_gs_coarse_levels", "mg_restrict", "mg_prolong", "mg_coarse_vcycle", "cg_start", "cg_dots",
+    "cg_dir_spmv", "cg_update", "diagnostics", "misc"};
+
+const double kRK4C[4] = {0.0, 0.5, 0.5, 1.0};
+const double kRK4W[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+
+struct Impl {
+    virtual ~Impl() {}
+    virtual void carve(Carver& cv) = 0;
+    virtual void init_phi(const double* phi0) = 0;
+    virtual void zero_state() = 0;
+    virtual pf_status step(int nsteps) = 0;
+    virtual pf_status project() = 0;
+    virtual pf_status diagnostics(pf_diag* out) = 0;
+    virtual pf_status get_field(int f, double* dst) = 0;
+    virtual pf_status set_field(int f, const double* src) = 0;
+    virtual size_t state_bytes() const = 0;
+    virtual pf_status get_state(void* dst) = 0;
+    virtual pf_status set_state(const void* src) = 0;
+    virtual pf_status eval_rhs(double gamma, double* kphi, double* ku) = 0;
+    virtual pf_status poisson_solve(const double* rhs, double* x, int* iters, double* relres) = 0;
+    virtual pf_status sync() = 0;
+    Prof prof;
+};
+
+}  // namespace
+
+namespace pf {
+void Prof::begin(int k) {
+    ++launches[k];
+    if (!timing) return;
+    if (!created) {
+        for (int i = 0; i < kPool; ++i) {
+            cudaEventCreate(&ev[i][0]);
+            cudaEventCreate(&ev[i][1]);
+        }
+        created = true;
+    }
+    if (used == kPool) harvest();
+    cls[used] = k;
+    cudaEventRecord(ev[used][0], st);
+}
+void Prof::end() {
+    if (!timing) return;
+    cudaEventRecord(ev[used][1], st);
+    ++used;
+}
+void Prof::harvest() {
+    if (!used) return;
+    cudaEventSynchronize(ev[used - 1][1]);
+    for (int i = 0; i < used; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[i][0], ev[i][1]) == cudaSuccess) ms[cls[i]] += t;
+    }
+    used = 0;
+}
+void Prof::destroy() {
+    if (!created) return;
+    for (int i = 0; i < kPool; ++i) {
+        cudaEventDestroy(ev[i][0]);
+        cudaEventDestroy(ev[i][1]);
+    }
+    created = false;
+}
+}  // namespace pf
+
+struct pf_ctx {
+    pf_params prm;
+    Impl* impl = nullptr;
+    std::string err;
+};
+
+namespace {
+
+pf_status validate(const pf_params* p, std::string& why) {
+    if (!p) { why = "params is NULL"; return PF_ERR_INVALID; }
+    if (p->dim != 2 && p->dim != 3) { why = "dim must be 2 or 3"; return PF_ERR_INVALID; }
+    long long nc = 1;
+    for (int d = 0; d < p->dim; ++d) {
+        if (p->n[d] < 4) { why = "each n[d] must be >= 4"; return PF_ERR_INVALID; }
+        nc *= p->n[d];
+    }
+    if (p->dim == 2 && p->n[2] != 1) { why = "n[2] must be 1 in 2D"; return PF_ERR_INVALID; }
+    if (nc > (1LL << 30)) { why = "grid too large (more than 2^30 cells)"; return PF_ERR_INVALID; }
+    if (p->model < 0 || p->model > 2) { why = "bad model"; return PF_ERR_INVALID; }
+    if (p->force < 0 || p->force > 2) { why = "bad force"; return PF_ERR_INVALID; }
+    if (p->precision < 0 || p->precision > 1) { why = "bad precision"; return PF_ERR_INVALID; }
+    if (p->scheme < 0 || p->scheme > 1) { why = "bad scheme"; return PF_ERR_INVALID; }
+    if (!(p->L > 0) || !(p->eps > 0) || !(p->dt > 0) || !(p->rho_in > 0) || !(p->rho_out > 0)) {
+        why = "L, eps, dt and densities must be positive";
+        return PF_ERR_INVALID;
+    }
+    if (p->mu_in < 0 || p->mu_out < 0 || p->sigma < 0 || p->delta_n < 0) {
+        why = "viscosities, sigma and delta_n must be non-negative";
+        return PF_ERR_INVALID;
+    }
+    if (!(p->poisson_rtol > 0) || p->poisson_maxit < 1) {
+        why = "poisson_rtol must be > 0 and poisson_maxit >= 1";
+        return PF_ERR_INVALID;
+    }
+    for (int i = 0; i < 8; ++i)
+        if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
+    return PF_OK;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+            return PF_ERR_CUDA;                                                          \
+        }                                                                                \
+    } while (0)
+
+template <typename T, int DIM>
+struct ImplT final : Impl {
+    pf_params prm;
+    Dims g;
+    Phys ph;
+    cudaStream_t st;
+    std::string& err;
+    // fields
+    T *phiN, *phiA, *phiB, *accphi;
+    T *uN[3], *uS[3], *uStar[3], *accu[3];
+    T *nrm[3], *aux;
+    double *p, *b, *r, *pd[2], *q;
+    T *rT, *z;
+    MGHier<T> H;
+    RedBuf rb;
+    CGScalars* sc;
+    double* gamma;
+    DiagOut* dout;
+    double* dsum;
+    // pinned host mirrors
+    CGScalars* h_sc = nullptr;
+    DiagOut* h_dout = nullptr;
+    double* h_scalar = nullptr;
+    long long nstep = 0;
+    double time = 0.0;
+    int last_iters = 0, max_iters = 0;
+    double last_relres = 0.0, last_gamma = 0.0;
+    int host_status = 0;
+
+    ImplT(const pf_params& p_, cudaStream_t s_, std::string& e_) : prm(p_), st(s_), err(e_) {
+        prof.st = s_;
+        g.nx = prm.n[0];
+        g.ny = prm.n[1];
+        g.nz = DIM == 3 ? prm.n[2] : 1;
+        g.ncell = g.nx * g.ny * g.nz;
+        g.h = prm.L / prm.n[0];
+        ph.dim = DIM;
+        ph.model = prm.model;
+        ph.force = prm.force;
+        ph.sigma = prm.sigma;
+        ph.eps = prm.eps;
+        ph.rho_in = prm.rho_in;
+        ph.rho_out = prm.rho_out;
+        ph.mu_in = prm.mu_in;
+        ph.mu_out = prm.mu_out;
+        ph.delta_n = prm.delta_n;
+        for (int d = 0; d < 3; ++d) uN[d] = uS[d] = uStar[d] = accu[d] = nrm[d] = nullptr;
+        // multigrid hierarchy geometry
+        H.nlev = 1;
+        H.lev[0].g = g;
+        while (H.nlev < kMaxLevels) {
+            const Dims& f = H.lev[H.nlev - 1].g;
+            bool ok = (f.nx % 2 == 0) && (f.ny % 2 == 0) && (DIM == 2 || f.nz % 2 == 0) &&
+                      f.nx >= 4 && f.ny >= 4 && (DIM == 2 || f.nz >= 4);
+            if (!ok) break;
+            Dims c;
+            c.nx = f.nx / 2;
+            c.ny = f.ny / 2;
+            c.nz = DIM == 3 ? f.nz / 2 : 1;
+            c.ncell = c.nx * c.ny * c.nz;
+            c.h = f.h * 2.0;
+            H.lev[H.nlev].g = c;
+            ++H.nlev;
+        }
+        H.first_coarse = H.nlev - 1;
+        for (int l = 0; l < H.nlev; ++l)
+            if (H.lev[l].g.ncell <= 4096) { H.first_coarse = l; break; }
+        H.pre = prm.mg_pre > 0 ? prm.mg_pre : 1;
+        H.post = prm.mg_post > 0 ? prm.mg_post : 1;
+        const Dims& cg = H.lev[H.nlev - 1].g;
+        int nmax = cg.nx > cg.ny ? cg.nx : cg.ny;
+        if (cg.nz > nmax) nmax = cg.nz;
+        int sweeps = 4 * nmax * nmax;
+        H.coarse_sweeps = sweeps < 8 ? 8 : (sweeps > 2000 ? 2000 : sweeps);
+    }
+
+    ~ImplT() override {
+        prof.destroy();
+        if (h_sc) cudaFreeHost(h_sc);
+        if (h_dout) cudaFreeHost(h_dout);
+        if (h_scalar) cudaFreeHost(h_scalar);
+    }
+
+    void carve(Carver& cv) override {
+        const size_t n = g.ncell;
+        phiN = cv.take<T>(n);
+        phiA = cv.take<T>(n);
+        phiB = cv.take<T>(n);
+        accphi = cv.take<T>(n);
+        for (int d = 0; d < DIM; ++d) {
+            uN[d] = cv.take<T>(n);
+            uS[d] = cv.take<T>(n);
+            uStar[d] = cv.take<T>(n);
+            accu[d] = cv.take<T>(n);
+            nrm[d] = cv.take<T>(n);
+        }
+        aux = cv.take<T>(2 * n);
+        p = cv.take<double>(n);
+        b = cv.take<double>(n);
+        r = cv.take<double>(n);
+        pd[0] = cv.take<double>(n);
+        pd[1] = cv.take<double>(n);
+        q = cv.take<double>(n);
+        if (sizeof(T) == sizeof(double)) {
+            rT = reinterpret_cast<T*>(r);
+        } else {
+            rT = cv.take<T>(n);
+        }
+        z = cv.take<T>(n);
+        H.lev[0].x = z;
+        H.lev[0].f = rT;
+        for (int d = 0; d < 3; ++d) H.lev[0].beta[d] = nullptr;
+        for (int l = 1; l < H.nlev; ++l) {
+            const size_t m = H.lev[l].g.ncell;
+            H.lev[l].x = cv.take<T>(m);
+            H.lev[l].f = cv.take<T>(m);
+            for (int d = 0; d < 3; ++d) H.lev[l].beta[d] = d < DIM ? cv.take<T>(m) : nullptr;
+        }
+        rb.part = cv.take<double>(kRedBlocks * 16);
+        rb.counter = cv.take<unsigned int>(4);
+        sc = cv.take<CGScalars>(1);
+        gamma = cv.take<double>(1);
+        dout = cv.take<DiagOut>(1);
+        dsum = cv.take<double>(4);
+    }
+
+    pf_status alloc_host() {
+        CK(cudaHostAlloc((void**)&h_sc, sizeof(CGScalars), cudaHostAllocDefault));
+        CK(cudaHostAlloc((void**)&h_dout, sizeof(DiagOut), cudaHostAllocDefault));
+        CK(cudaHostAlloc((void**)&h_scalar, 8 * sizeof(double), cudaHostAllocDefault));
+        return PF_OK;
+    }
+
+    pf_status init_device() {
+        const size_t n = g.ncell;
+        // zero everything that must start at zero
+        for (int d = 0; d < DIM; ++d) {
+            CK(cudaMemsetAsync(uN[d], 0, n * sizeof(T), st));
+            CK(cudaMemsetAsync(uS[d], 0, n * sizeof(T), st));
+            CK(cudaMemsetAsync(uStar[d], 0, n * sizeof(T), st));
+            CK(cudaMemsetAsync(accu[d], 0, n * sizeof(T), st));
+        }
+        CK(cudaMemsetAsync(p, 0, n * sizeof(double), st));
+        CK(cudaMemsetAsync(q, 0, n * sizeof(double), st));
+        CK(cudaMemsetAsync(pd[0], 0, n * sizeof(double), st));
+        CK(cudaMemsetAsync(pd[1], 0, n * sizeof(double), st));
+        CK(cudaMemsetAsync(aux, 0, 2 * n * sizeof(T), st));
+        CK(cudaMemsetAsync(rb.counter, 0, 4 * sizeof(unsigned int), st));
+        CGScalars s0;
+        memset(&s0, 0, sizeof(s0));
+        s0.rtol2 = prm.poisson_rtol * prm.poisson_rtol;
+        s0.maxit = prm.poisson_maxit;
+        *h_sc = s0;
+        CK(cudaMemcpyAsync(sc, h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(gamma, 0, sizeof(double), st));
+        CK(cudaStreamSynchronize(st));
+        return PF_OK;
+    }
+
+    void init_phi(const double* phi0) override {
+        if (phi0) {
+            // stage through b (float64 device buffer) so host or device sources work
+            cudaMemcpyAsync(b, phi0, g.ncell * sizeof(double), cudaMemcpyDefault, st);
+            launch_convert_in<T>(b, phiN, g.ncell, st);
+        } else {
+            launch_init_phi<T, DIM>(g, ph, prm.R, prm.pert_mode, prm.pert_amp, phiN, st);
+        }
+    }
+
+    void zero_state() override {}
+
+    // ---------------- projection ----------------
+    // u_out = u_in - tau beta G p with D(beta G p) = D u_in / tau (phi -> rho)
+    pf_status do_project(const T* phi, T* const* uin, double tau, T* const* uout) {
+        const T* uin_c[3] = {uin[0], uin[1], DIM == 3 ? uin[2] : uin[0]};
+        prof.begin(KC_DIV);
+        launch_divergence<T, DIM>(g, uin_c, 1.0 / tau, b, rb, sc, st);
+        prof.end();
+        pf_status s = solve(phi, -1.0);
+        if (s != PF_OK) return s;
+        prof.begin(KC_CORRECT);
+        launch_correct<T, DIM>(g, ph, phi, uin_c, p, tau, uout, st);
+        prof.end();
+        return PF_OK;
+    }
+
+    // CG on A p = sign (b - mean b), warm start from p
+    pf_status solve(const T* phi, double sign) {
+        prof.begin(KC_COARSEN);
+        launch_mg_setup<T, DIM>(g, ph, phi, H, st);
+        prof.end();
+        prof.begin(KC_CG_START);
+        launch_cg_start<T, DIM>(g, ph, phi, b, sign, p, r, rT, rb, sc, st);
+        prof.end();
+        int cur = 0;
+        const int maxit = prm.poisson_maxit;
+        int it = 0;
+        int poll = 1;
+        while (it < maxit) {
+            const int first = (it == 0);
+            launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof);
+            prof.begin(KC_CG_DOTS);
+            launch_cg_dots<T, DIM>(g, z, r, q, first, rb, sc, st);
+            prof.end();
+            prof.begin(KC_CG_DIR);
+            launch_cg_dir<T, DIM>(g, ph, phi, z, pd[cur], pd[1 - cur], q, first, rb, sc, st);
+            prof.end();
+            prof.begin(KC_CG_UPDATE);
+            launch_cg_update<T, DIM>(g, pd[1 - cur], q, p, r, rT, rb, sc, st);
+            prof.end();
+            cur = 1 - cur;
+            ++it;
+            if (it % poll == 0 || it == maxit) {
+                CK(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                prof.harvest();
+                if (h_sc->done) break;
+            }
+        }
+        CK(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        last_iters = h_sc->iters;
+        if (last_iters > max_iters) max_iters = last_iters;
+        last_relres = h_sc->ff > 0 ? sqrt(h_sc->rr / h_sc->ff) : 0.0;
+        if (h_sc->status) {
+            int stt = h_sc->status;
+            h_sc->status = 0;
+            CK(cudaMemsetAsync(&sc->status, 0, sizeof(int), st));
+            err = stt == PF_ERR_NOT_CONVERGED ? "Poisson solve reached poisson_maxit"
+                                              : "non-finite value in the Poisson solve";
+            return (pf_status)stt;
+        }
+        return PF_OK;
+    }
+
+    // ---------------- one step ----------------
+    pf_status one_step() {
+        const double dt = prm.dt;
+        const T* uNc[3] = {uN[0], uN[1], DIM == 3 ? uN[2] : uN[0]};
+        prof.begin(KC_GAMMA);
+        launch_gamma<T, DIM>(g, uNc, prm.gamma_fixed, prm.gamma_min, gamma, rb, st);
+        prof.end();
+        StageIO<T> io;
+        memset(&io, 0, sizeof(io));
+        io.phi_n = phiN;
+        io.acc_phi = accphi;
+        io.gamma = gamma;
+        io.aux = aux;
+        for (int d = 0; d < 3; ++d) {
+            io.u_n[d] = uN[d];
+            io.acc_u[d] = accu[d];
+            io.u_out[d] = uStar[d];
+            io.nrm[d] = nrm[d];
+        }
+        if (prm.scheme == PF_FE) {
+            io.phi_s = phiN;
+            for (int d = 0; d < 3; ++d) io.u_s[d] = uN[d];
+            io.phi_out = phiA;
+            prof.begin(KC_CELL);
+            launch_cell_pass<T, DIM>(g, ph, phiN, nrm[0], nrm[1], nrm[2], aux, st);
+            prof.end();
+            prof.begin(KC_STAGE);
+            launch_stage<T, DIM>(g, ph, io, 0, 1, dt, dt, 0, st);
+            prof.end();
+            pf_status s = do_project(phiA, uStar, dt, uN);
+            T* t = phiN;
+            phiN = phiA;
+            phiA = t;
+            return s;
+        }
+        T* phin_s[4] = {phiN, phiA, phiB, phiA};
+        T* phout[4] = {phiA, phiB, phiA, phiN};
+        for (int s = 0; s < 4; ++s) {
+            io.phi_s = phin_s[s];
+            for (int d = 0; d < 3; ++d) io.u_s[d] = s == 0 ? uN[d] : uS[d];
+            io.phi_out = phout[s];
+            prof.begin(KC_CELL);
+            launch_cell_pass<T, DIM>(g, ph, phin_s[s], nrm[0], nrm[1], nrm[2], aux, st);
+            prof.end();
+            const double wdt = kRK4W[s] * dt;
+            const double cdt = s < 3 ? kRK4C[s + 1] * dt : dt;
+            prof.begin(KC_STAGE);
+            launch_stage<T, DIM>(g, ph, io, s, 0, wdt, cdt, 0, st);
+            prof.end();
+            pf_status ps = do_project(phout[s], uStar, cdt, s < 3 ? uS : uN);
+            if (ps != PF_OK) return ps;
+        }
+        return PF_OK;
+    }
+
+    pf_status step(int nsteps) override {
+        for (int k = 0; k < nsteps; ++k) {
+            pf_status s = one_step();
+            if (s != PF_OK) return s;
+            ++nstep;
+            time += prm.dt;
+        }
+        CK(cudaMemcpyAsync(h_scalar, gamma, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        last_gamma = h_scalar[0];
+        CK(cudaGetLastError());
+        return PF_OK;
+    }
+
+    pf_status project() override {
+        pf_status s = do_project(phiN, uN, prm.dt, uN);
+        if (s != PF_OK) return s;
+        CK(cudaStreamSynchronize(st));
+        return PF_OK;
+    }
+
+    pf_status diagnostics(pf_diag* out) override {
+        const T* uNc[3] = {uN[0], uN[1], DIM == 3 ? uN[2] : uN[0]};
+        prof.begin(KC_DIAG);
+        launch_diagnostics<T, DIM>(g, ph, phiN, uNc, p, rb, dout, st);
+        prof.end();
+        CK(cudaMemcpyAsync(h_dout, dout, sizeof(DiagOut), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        const DiagOut& d = *h_dout;
+        memset(out, 0, sizeof(*out));
+        out->mass = d.mass;
+        out->ke = d.ke;
+        out->se = d.se;
+        out->umax = d.umax;
+        out->ca_inf = prm.sigma > 0 ? d.umax * prm.mu_in / prm.sigma : 0.0;
+        out->dp_laplace = (d.n_in > 0 && d.n_out > 0) ? d.p_in_sum / d.n_in - d.p_out_sum / d.n_out
+                                                      : 0.0;
+        out->phi_min = d.phi_min;
+        out->phi_max = d.phi_max;
+        out->poisson_relres = last_relres;
+        out->poisson_iters = last_iters;
+        out->poisson_iters_max = max_iters;
+        out->gamma = last_gamma;
+        out->step = nstep;
+        out->t = time;
+        max_iters = 0;
+        if (d.nonfinite > 0) {
+            err = "non-finite value in the state";
+            return PF_ERR_NONFINITE;
+        }
+        if (prm.bound_tol > 0 && (d.phi_min < -prm.bound_tol || d.phi_max > 1.0 + prm.bound_tol)) {
+            err = "phi left [-bound_tol, 1 + bound_tol]";
+            return PF_ERR_UNBOUNDED;
+        }
+        return PF_OK;
+    }
+
+    T* field_ptr(int f) {
+        switch (f) {
+            case PF_FIELD_PHI: return phiN;
+            case PF_FIELD_U: return uN[0];
+            case PF_FIELD_V: return uN[1];
+            case PF_FIELD_W: return DIM == 3 ? uN[2] : nullptr;
+            default: return nullptr;
+        }
+    }
+
+    pf_status get_field(int f, double* dst) override {
+        if (!dst) { err = "dst is NULL"; return PF_ERR_INVALID; }
+        const size_t bytes = (size_t)g.ncell * sizeof(double);
+        if (f == PF_FIELD_P) {
+            launch_sum(g.ncell, p, rb, dsum, st);
+            launch_convert_out<double>(p, b, g.ncell, 0.0, dsum, 1.0 / g.ncell, st);
+        } else {
+            T* src = field_ptr(f);
+            if (!src) { err = "bad field id"; return PF_ERR_INVALID; }
+            launch_convert_out<T>(src, b, g.ncell, 0.0, nullptr, 0.0, st);
+        }
+        CK(cudaMemcpyAsync(dst, b, bytes, cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        return PF_OK;
+    }
+
+    pf_status set_field(int f, const double* src) override {
+        if (!src) { err = "src is NULL"; return PF_ERR_INVALID; }
+        const size_t bytes = (size_t)g.ncell * sizeof(double);
+        CK(cudaMemcpyAsync(b, src, bytes, cudaMemcpyDefault, st));
+        if (f == PF_FIELD_P) {
+            CK(cudaMemcpyAsync(p, b, bytes, cudaMemcpyDeviceToDevice, st));
+        } else {
+            T* dstp = field_ptr(f);
+            if (!dstp) { err = "bad field id"; return PF_ERR_INVALID; }
+            launch_convert_in<T>(b, dstp, g.ncell, st);
+        }
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        return PF_OK;
+    }
+
+    size_t state_bytes() const override {
+        return (size_t)g.ncell * ((1 + DIM) * sizeof(T) + sizeof(double)) + 2 * sizeof(double);
+    }
+
+    pf_status get_state(void* dst) override {
+        if (!dst) { err = "dst is NULL"; return PF_ERR_INVALID; }
+        char* o = static_cast<char*>(dst);
+        const size_t nT = (size_t)g.ncell * sizeof(T);
+        CK(cudaMemcpyAsync(o, phiN, nT, cudaMemcpyDefault, st));
+        o += nT;
+        for (int d = 0; d < DIM; ++d) {
+            CK(cudaMemcpyAsync(o, uN[d], nT, cudaMemcpyDefault, st));
+            o += nT;
+        }
+        CK(cudaMemcpyAsync(o, p, (size_t)g.ncell * sizeof(double), cudaMemcpyDefault, st));
+        o += (size_t)g.ncell * sizeof(double);
+        h_scalar[0] = (double)nstep;
+        h_scalar[1] = time;
+        CK(cudaMemcpyAsync(o, h_scalar, 2 * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        return PF_OK;
+    }
+
+    pf_status set_state(const void* src) override {
+        if (!src) { err = "src is NULL"; return PF_ERR_INVALID; }
+        const char* o = static_cast<const char*>(src);
+        const size_t nT = (size_t)g.ncell * sizeof(T);
+        CK(cudaMemcpyAsync(phiN, o, nT, cudaMemcpyDefault, st));
+        o += nT;
+        for (int d = 0; d < DIM; ++d) {
+            CK(cudaMemcpyAsync(uN[d], o, nT, cudaMemcpyDefault, st));
+            o += nT;
+        }
+        CK(cudaMemcpyAsync(p, o, (size_t)g.ncell * sizeof(double), cudaMemcpyDefault, st));
+        o += (size_t)g.ncell * sizeof(double);
+        CK(cudaMemcpyAsync(h_scalar, o, 2 * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        nstep = (long long)h_scalar[0];
+        time = h_scalar[1];
+        return PF_OK;
+    }
+
+    pf_status eval_rhs(double gam, double* kphi, double* ku) override {
+        if (!kphi || !ku) { err = "NULL output"; return PF_ERR_INVALID; }
+        h_scalar[2] = gam;
+        CK(cudaMemcpyAsync(gamma, h_scalar + 2, sizeof(double), cudaMemcpyHostToDevice, st));
+        StageIO<T> io;
+        memset(&io, 0, sizeof(io));
+        io.phi_s = phiN;
+        io.phi_n = phiN;
+        io.acc_phi = accphi;
+        io.gamma = gamma;
+        io.aux = aux;
+        io.phi_out = phiA;
+        for (int d = 0; d < 3; ++d) {
+            io.u_s[d] = uN[d];
+            io.u_n[d] = uN[d];
+            io.acc_u[d] = accu[d];
+            io.u_out[d] = uStar[d];
+            io.nrm[d] = nrm[d];
+        }
+        // outputs staged in float64 device buffers: kphi -> b, ku -> pd[0], pd[1], q
+        io.rhs_phi = b;
+        io.rhs_u[0] = pd[0];
+        io.rhs_u[1] = pd[1];
+        io.rhs_u[2] = q;
+        launch_cell_pass<T, DIM>(g, ph, phiN, nrm[0], nrm[1], nrm[2], aux, st);
+        launch_stage<T, DIM>(g, ph, io, 0, 0, 0.0, 0.0, 1, st);
+        const size_t bytes = (size_t)g.ncell * sizeof(double);
+        CK(cudaMemcpyAsync(kphi, b, bytes, cudaMemcpyDefault, st));
+        for (int d = 0; d < DIM; ++d)
+            CK(cudaMemcpyAsync(ku + (size_t)d * g.ncell, io.rhs_u[d], bytes, cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        return PF_OK;
+    }
+
+    pf_status poisson_solve(const double* rhs, double* x, int* iters, double* relres) override {
+        if (!rhs || !x) { err = "NULL pointer"; return PF_ERR_INVALID; }
+        const size_t bytes = (size_t)g.ncell * sizeof(double);
+        CK(cudaMemcpyAsync(b, rhs, bytes, cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(p, x, bytes, cudaMemcpyDefault, st));
+        launch_sum(g.ncell, b, rb, dsum, st);
+        // mean_b = sum / n, written into the scalars
+        CK(cudaMemcpyAsync(h_scalar + 3, dsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        h_scalar[4] = h_scalar[3] / g.ncell;
+        CK(cudaMemcpyAsync(&sc->mean_b, h_scalar + 4, sizeof(double), cudaMemcpyHostToDevice, st));
+        pf_status s = solve(phiN, 1.0);
+        if (iters) *iters = last_iters;
+        if (relres) *relres = last_relres;
+        if (s != PF_OK && s != PF_ERR_NOT_CONVERGED) return s;
+        launch_sum(g.ncell, p, rb, dsum, st);
+        launch_convert_out<double>(p, b, g.ncell, 0.0, dsum, 1.0 / g.ncell, st);
+        CK(cudaMemcpyAsync(x, b, bytes, cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        return s;
+    }
+
+    pf_status sync() override {
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        return PF_OK;
+    }
+};
+
+Impl* make_impl(const pf_params& p, cudaStream_t s, std::string& err) {
+    const bool mixed = p.precision == PF_MIXED;
+    if (p.dim == 2) {
+        if (mixed) return new (std::nothrow) ImplT<float, 2>(p, s, err);
+        return new (std::nothrow) ImplT<double, 2>(p, s, err);
+    }
+    if (mixed) return new (std::nothrow) ImplT<float, 3>(p, s, err);
+    return new (std::nothrow) ImplT<double, 3>(p, s, err);
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_workspace_size(const pf_params* prm, size_t* bytes) {
+    std::string why;
+    pf_status s = validate(prm, why);
+    if (s != PF_OK) { g_init_error = why; return s; }
+    if (!bytes) { g_init_error = "bytes is NULL"; return PF_ERR_INVALID; }
+    std::string err;
+    Impl* im = make_impl(*prm, nullptr, err);
+    if (!im) return PF_ERR_INVALID;
+    Carver cv{nullptr};
+    im->carve(cv);
+    *bytes = cv.off;
+    delete im;
+    return PF_OK;
+}
+
+pf_status pf_init(const pf_params* prm, void* workspace, size_t workspace_bytes, const double* phi0,
+                  void* stream, pf_ctx** out) {
+    std::string why;
+    if (!out) { g_init_error = "out is NULL"; return PF_ERR_INVALID; }
+    *out = nullptr;
+    pf_status s = validate(prm, why);
+    if (s != PF_OK) { g_init_error = why; return s; }
+    size_t need = 0;
+    pf_workspace_size(prm, &need);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 ||
+        workspace_bytes < need) {
+        g_init_error = "workspace NULL, not 256-byte aligned or smaller than pf_workspace_size";
+        return PF_ERR_WORKSPACE;
+    }
+    pf_ctx* ctx = new (std::nothrow) pf_ctx();
+    if (!ctx) { g_init_error = "out of host memory"; return PF_ERR_INVALID; }
+    ctx->prm = *prm;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Impl* im = make_impl(*prm, st, ctx->err);
+    if (!im) { delete ctx; g_init_error = "out of host memory"; return PF_ERR_INVALID; }
+    ctx->impl = im;
+    Carver cv{static_cast<char*>(workspace)};
+    im->carve(cv);
+    pf_status hs;
+    if (prm->dim == 2) {
+        hs = prm->precision == PF_MIXED ? static_cast<ImplT<float, 2>*>(im)->alloc_host()
+                                        : static_cast<ImplT<double, 2>*>(im)->alloc_host();
+        if (hs == PF_OK)
+            hs = prm->precision == PF_MIXED ? static_cast<ImplT<float, 2>*>(im)->init_device()
+                                            : static_cast<ImplT<double, 2>*>(im)->init_device();
+    } else {
+        hs = prm->precision == PF_MIXED ? static_cast<ImplT<float, 3>*>(im)->alloc_host()
+                                        : static_cast<ImplT<double, 3>*>(im)->alloc_host();
+        if (hs == PF_OK)
+            hs = prm->precision == PF_MIXED ? static_cast<ImplT<float, 3>*>(im)->init_device()
+                                            : static_cast<ImplT<double, 3>*>(im)->init_device();
+    }
+    if (hs != PF_OK) {
+        g_init_error = ctx->err;
+        delete im;
+        delete ctx;
+        return hs;
+    }
+    im->init_phi(phi0);
+    s = im->sync();
+    if (s != PF_OK) {
+        g_init_error = ctx->err;
+        delete im;
+        delete ctx;
+        return s;
+    }
+    *out = ctx;
+    return PF_OK;
+}
+
+pf_status pf_step(pf_ctx* ctx, int nsteps) {
+    if (!ctx || nsteps < 0) return PF_ERR_INVALID;
+    return ctx->impl->step(nsteps);
+}
+
+pf_status pf_project(pf_ctx* ctx) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->project();
+}
+
+pf_status pf_diagnostics(pf_ctx* ctx, pf_diag* out) {
+    if (!ctx || !out) return PF_ERR_INVALID;
+    return ctx->impl->diagnostics(out);
+}
+
+pf_status pf_get_field(pf_ctx* ctx, int field, double* dst) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->get_field(field, dst);
+}
+
+pf_status pf_set_field(pf_ctx* ctx, int field, const double* src) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->set_field(field, src);
+}
+
+size_t pf_state_bytes(const pf_ctx* ctx) { return ctx ? ctx->impl->state_bytes() : 0; }
+
+pf_status pf_get_state(pf_ctx* ctx, void* dst) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->get_state(dst);
+}
+
+pf_status pf_set_state(pf_ctx* ctx, const void* src) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->set_state(src);
+}
+
+pf_status pf_eval_rhs(pf_ctx* ctx, double gamma, double* kphi, double* ku) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->eval_rhs(gamma, kphi, ku);
+}
+
+pf_status pf_poisson_solve(pf_ctx* ctx, const double* rhs, double* x, int* iters,
+                           double* relres) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->poisson_solve(rhs, x, iters, relres);
+}
+
+pf_status pf_profile_enable(pf_ctx* ctx, int enable) {
+    if (!ctx) return PF_ERR_INVALID;
+    ctx->impl->sync();
+    ctx->impl->prof.harvest();
+    ctx->impl->prof.timing = enable != 0;
+    return PF_OK;
+}
+
+int pf_profile_read(pf_ctx* ctx, pf_profile_entry* out, int max_entries, int reset) {
+    if (!ctx) return -1;
+    Prof& pr = ctx->impl->prof;
+    ctx->impl->sync();
+    pr.harvest();
+    int n = 0;
+    for (int k = 0; k < KC_COUNT; ++k) {
+        if (out && n < max_entries) {
+            out[n].name = kClassNames[k];
+            out[n].launches = pr.launches[k];
+            out[n].ms = pr.ms[k];
+        }
+        ++n;
+    }
+    if (reset) {
+        for (int k = 0; k < KC_COUNT; ++k) {
+            pr.launches[k] = 0;
+            pr.ms[k] = 0.0;
+        }
+    }
+    return n;
+}
+
+pf_status pf_sync(pf_ctx* ctx) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->sync();
+}
+
+void pf_destroy(pf_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->impl) {
+        ctx->impl->sync();
+        delete ctx->impl;
+    }
+    delete ctx;
+}
+
+const char* pf_last_error(const pf_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,539 @@
+// Stage kernels of the fractional step: initial profile, the cell pass
+// (normals, curvature, chemical potential), the fused phase-field +
+// momentum right-hand side with the RK stage update, Gamma, divergence,
+// velocity correction and diagnostics.
+//
+// Discretization (uniform periodic staggered grid, face i-1/2 stored at i):
+//   phase field   d phi/dt + div(u phi) = g(phi), g from Table 1 (CDI, SB, ISODI)
+//   chemical pot. mu = (6 sigma/eps) psi'(phi) - 6 sigma eps lap(phi)      (Eq. ac_mu)
+//   EB force      F = mu_f (phi_i - phi_{i-1}) / h                         (Eq. eb_st)
+//   CSF / LCSF    F = sigma kappa_f dphi, 6 sigma kappa_f phi_f(1-phi_f) dphi (Section 2)
+//   momentum      du/dt = -(u.grad)u + div(eta (grad u + grad u^T))/rho_f + F/rho_f
+#include "pf_device.cuh"
+
+namespace pf {
+
+template <typename T>
+__device__ __forceinline__ T clamp01(T v) { return v < T(0) ? T(0) : (v > T(1) ? T(1) : v); }
+
+template <typename T>
+__device__ __forceinline__ T rho_of(T phi, const Phys& ph) {
+    return T(ph.rho_out) + (T(ph.rho_in) - T(ph.rho_out)) * clamp01(phi);
+}
+
+template <typename T>
+__device__ __forceinline__ T eta_of(T phi, const Phys& ph) {
+    return T(ph.mu_out) + (T(ph.mu_in) - T(ph.mu_out)) * clamp01(phi);
+}
+
+// psi'(phi) = phi (1 - phi) (1 - 2 phi), always evaluated in float64.
+__device__ __forceinline__ double dpsi64(double p) { return p * (1.0 - p) * (1.0 - 2.0 * p); }
+
+// ---------------------------------------------------------------------------
+// initial profile phi0 = [1 + tanh((R(theta) - r) / (2 eps))] / 2
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_init_phi(Dims g, Phys ph, double R, int mode, double amp, T* __restrict__ phi) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.ncell) return;
+    Cell c = decode(idx, g);
+    double cx = 0.5 * g.nx * g.h, cy = 0.5 * g.ny * g.h, cz = 0.5 * g.nz * g.h;
+    double x = (c.i + 0.5) * g.h - cx, y = (c.j + 0.5) * g.h - cy;
+    double z = DIM == 3 ? (c.k + 0.5) * g.h - cz : 0.0;
+    double r = sqrt(x * x + y * y + z * z);
+    double Rt = R;
+    if (mode > 0 && amp != 0.0) {
+        if (DIM == 2) {
+            Rt = R * (1.0 + amp * cos(mode * atan2(y, x)));
+        } else {
+            double ct = r > 0.0 ? z / r : 1.0;
+            // Legendre P_mode(ct) by the three-term (Bonnet) recurrence
+            double p0 = 1.0, p1 = ct;
+            for (int l = 1; l < mode; ++l) {
+                double p2 = ((2 * l + 1) * ct * p1 - l * p0) / (l + 1);
+                p0 = p1;
+                p1 = p2;
+            }
+            Rt = R * (1.0 + amp * (mode == 0 ? 1.0 : p1));
+        }
+    }
+    phi[idx] = T(0.5 * (1.0 + tanh((Rt - r) / (2.0 * ph.eps))));
+}
+
+template <typename T, int DIM>
+void launch_init_phi(const Dims& g, const Phys& ph, double R, int mode, double amp, T* phi,
+                     cudaStream_t s) {
+    k_init_phi<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(g, ph, R, mode, amp, phi);
+}
+
+template <typename T>
+__global__ void k_convert_in(const double* __restrict__ src, T* __restrict__ dst, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = T(src[i]);
+}
+
+template <typename T>
+__global__ void k_convert_out(const T* __restrict__ src, double* __restrict__ dst, int n,
+                              const double* sum_ptr, double inv_n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double m = sum_ptr ? (*sum_ptr) * inv_n : 0.0;
+    if (i < n) dst[i] = double(src[i]) - m;
+}
+
+template <typename T>
+void launch_convert_in(const double* src, T* dst, int n, cudaStream_t s) {
+    k_convert_in<T><<<lin_grid(n), kThreads, 0, s>>>(src, dst, n);
+}
+
+template <typename T>
+void launch_convert_out(const T* src, double* dst, int n, double, const double* sum_ptr,
+                        double inv_n, cudaStream_t s) {
+    k_convert_out<T><<<lin_grid(n), kThreads, 0, s>>>(src, dst, n, sum_ptr, inv_n);
+}
+
+// ---------------------------------------------------------------------------
+// cell pass: normals n = grad_c phi / (|grad_c phi| + delta_n), and mu (EB
+// force) and/or kappa = -div_c n (CSF, LCSF, SB, ISODI)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__device__ __forceinline__ void normal_at(const T* __restrict__ phi, const Nbr<DIM>& nb, int oi,
+                                          int oj, int ok, T inv2h, T dn, T (&n)[3], T& mag) {
+    T gr[3];
+    gr[0] = (ldg(phi, nb.at(oi + 1, oj, ok)) - ldg(phi, nb.at(oi - 1, oj, ok))) * inv2h;
+    gr[1] = (ldg(phi, nb.at(oi, oj + 1, ok)) - ldg(phi, nb.at(oi, oj - 1, ok))) * inv2h;
+    gr[2] = DIM == 3 ? (ldg(phi, nb.at(oi, oj, ok + 1)) - ldg(phi, nb.at(oi, oj, ok - 1))) * inv2h
+                     : T(0);
+    T s = gr[0] * gr[0] + gr[1] * gr[1];
+    if (DIM == 3) s += gr[2] * gr[2];
+    mag = sqrt(s);
+    T den = mag + dn;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) n[d] = gr[d] / den;
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* __restrict__ n1,
+            T* __restrict__ n2, T* __restrict__ mu_out, T* __restrict__ kap_out) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.ncell) return;
+    Cell c = decode(idx, g);
+    Nbr<DIM> nb(c, g);
+    const T inv_h = T(1.0 / g.h), inv2h = T(0.5 / g.h), inv_h2 = T(1.0 / (g.h * g.h));
+    const T dn = T(ph.delta_n);
+    T n[3], mag;
+    normal_at<T, DIM>(phi, nb, 0, 0, 0, inv2h, dn, n, mag);
+    n0[idx] = n[0];
+    n1[idx] = n[1];
+    if (DIM == 3) n2[idx] = n[2];
+    const T pc = ldg(phi, idx);
+    if (mu_out) {
+        T lap = T(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+            lap = lap + (ldg(phi, nb.ax(d, 1)) - T(2) * pc + ldg(phi, nb.ax(d, -1))) * inv_h2;
+        const double sh = 6.0 * ph.sigma;
+        // double-well term in float64 (cancellation near phi = 0, 1)
+        double mu = (sh / ph.eps) * dpsi64(double(pc)) - sh * ph.eps * double(lap);
+        mu_out[idx] = T(mu);
+    }
+    if (kap_out) {
+        T div = T(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            T np_[3], nm_[3], mg;
+            int oi = d == 0, oj = d == 1, ok = d == 2;
+            normal_at<T, DIM>(phi, nb, oi, oj, ok, inv2h, dn, np_, mg);
+            normal_at<T, DIM>(phi, nb, -oi, -oj, -ok, inv2h, dn, nm_, mg);
+            div = div + (np_[d] - nm_[d]) * inv2h;
+        }
+        kap_out[idx] = -div;
+    }
+    (void)inv_h;
+}
+
+template <typename T, int DIM>
+void launch_cell_pass(const Dims& g, const Phys& ph, const T* phi, T* nrm0, T* nrm1, T* nrm2,
+                      T* aux, cudaStream_t s) {
+    // aux holds mu for the EB force, kappa otherwise; kappa for SB/ISODI with the
+    // EB force is stored after the mu array (aux + ncell).
+    T* mu = nullptr;
+    T* kap = nullptr;
+    if (ph.force == 0) {
+        mu = aux;
+        if (ph.model != 0) kap = aux + g.ncell;
+    } else {
+        kap = aux;
+    }
+    k_cell_pass<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(g, ph, phi, nrm0, nrm1, nrm2, mu,
+                                                                kap);
+}
+
+// ---------------------------------------------------------------------------
+// fused stage kernel: phase-field rhs at the cell, momentum rhs at the cell's
+// low faces, and the RK stage update of both
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int write_rhs) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.ncell) return;
+    Cell c = decode(idx, g);
+    Nbr<DIM> nb(c, g);
+    const T h = T(g.h), inv_h = T(1.0 / g.h), inv2h = T(0.5 / g.h), inv_h2 = T(1.0 / (g.h * g.h));
+    const T eps = T(ph.eps);
+    const T gam = T(*io.gamma);
+    const T* __restrict__ phi = io.phi_s;
+    const T pc = ldg(phi, idx);
+
+    // ---------------- phase field (Eq. 1, Table 1) ----------------
+    T kphi = T(0);
+    if (ph.model == 0) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const T* __restrict__ nd = io.nrm[d];
+            const T* __restrict__ ud = io.u_s[d];
+            // low face (between c - e_d and c)
+            T pm = ldg(phi, nb.ax(d, -1));
+            T pf = T(0.5) * (pc + pm);
+            T nf = T(0.5) * (ldg(nd, idx) + ldg(nd, nb.ax(d, -1)));
+            T Flo = ldg(ud, idx) * pf - gam * (eps * ((pc - pm) * inv_h) - pf * (T(1) - pf) * nf);
+            // high face (between c and c + e_d)
+            int ip = nb.ax(d, 1);
+            T pp = ldg(phi, ip);
+            T pf2 = T(0.5) * (pp + pc);
+            T nf2 = T(0.5) * (ldg(nd, ip) + ldg(nd, idx));
+            T Fhi = ldg(ud, ip) * pf2 - gam * (eps * ((pp - pc) * inv_h) - pf2 * (T(1) - pf2) * nf2);
+            kphi = kphi - (Fhi - Flo) * inv_h;
+        }
+    } else {
+        T lap = T(0), g2 = T(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const T* __restrict__ ud = io.u_s[d];
+            T pm = ldg(phi, nb.ax(d, -1));
+            int ip = nb.ax(d, 1);
+            T pp = ldg(phi, ip);
+            T Flo = ldg(ud, idx) * (T(0.5) * (pc + pm));
+            T Fhi = ldg(ud, ip) * (T(0.5) * (pp + pc));
+            kphi = kphi - (Fhi - Flo) * inv_h;
+            lap = lap + (pp - T(2) * pc + pm) * inv_h2;
+            T gd = (pp - pm) * inv2h;
+            g2 = g2 + gd * gd;
+        }
+        const T* kap = (ph.force == 0) ? io.aux + g.ncell : io.aux;
+        T kc = ldg(kap, idx);
+        T third = (ph.model == 1) ? eps * sqrt(g2) * kc : pc * (T(1) - pc) * kc;
+        T dp = T(dpsi64(double(pc)));
+        kphi = kphi + gam * (eps * lap - dp / eps + third);
+    }
+
+    // ---------------- momentum at the low faces ----------------
+    T ku[3];
+    const T sigma = T(ph.sigma);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const T* __restrict__ ud = io.u_s[d];
+        const int im = nb.ax(d, -1);
+        const T pm = ldg(phi, im);
+        const T udc = ldg(ud, idx);
+        // advection -(u.grad) u_d, central, transverse components from 4 faces
+        T adv = T(0);
+#pragma unroll
+        for (int e = 0; e < DIM; ++e) {
+            T vel;
+            if (e == d) {
+                vel = udc;
+            } else {
+                const T* __restrict__ ue = io.u_s[e];
+                vel = T(0.25) * (ldg(ue, idx) + ldg(ue, nb.ax(e, 1)) + ldg(ue, im) +
+                                 ldg(ue, nb.ax2(d, -1, e, 1)));
+            }
+            adv = adv + vel * ((ldg(ud, nb.ax(e, 1)) - ldg(ud, nb.ax(e, -1))) * inv2h);
+        }
+        // viscous stress divergence
+        T visc = T(0);
+        const T etac = eta_of(pc, ph), etam = eta_of(pm, ph);
+#pragma unroll
+        for (int e = 0; e < DIM; ++e) {
+            if (e == d) {
+                T thi = T(2) * etac * ((ldg(ud, nb.ax(d, 1)) - udc) * inv_h);
+                T tlo = T(2) * etam * ((udc - ldg(ud, im)) * inv_h);
+                visc = visc + (thi - tlo) * inv_h;
+            } else {
+                const T* __restrict__ ue = io.u_s[e];
+                // edge at (c - e_d/2 - e_e/2): cells c, c-e_d, c-e_e, c-e_d-e_e
+                T eta_lo = T(0.25) * (etac + etam + eta_of(ldg(phi, nb.ax(e, -1)), ph) +
+                                      eta_of(ldg(phi, nb.ax2(d, -1, e, -1)), ph));
+                T tlo = eta_lo * ((udc - ldg(ud, nb.ax(e, -1))) * inv_h +
+                                  (ldg(ue, idx) - ldg(ue, im)) * inv_h);
+                // edge at (c - e_d/2 + e_e/2): cells c+e_e, c+e_e-e_d, c, c-e_d
+                const int iep = nb.ax(e, 1), iepm = nb.ax2(d, -1, e, 1);
+                T eta_hi = T(0.25) * (eta_of(ldg(phi, iep), ph) + eta_of(ldg(phi, iepm), ph) +
+                                      etac + etam);
+                T thi = eta_hi * ((ldg(ud, iep) - udc) * inv_h +
+                                  (ldg(ue, iep) - ldg(ue, iepm)) * inv_h);
+                visc = visc + (thi - tlo) * inv_h;
+            }
+        }
+        // surface tension force at the face
+        const T dphi = (pc - pm) * inv_h;
+        T F;
+        if (ph.force == 0) {
+            F = T(0.5) * (ldg(io.aux, idx) + ldg(io.aux, im)) * dphi;
+        } else {
+            T kf = T(0.5) * (ldg(io.aux, idx) + ldg(io.aux, im));
+            if (ph.force == 1) {
+                F = sigma * kf * dphi;
+            } else {
+                T pf = T(0.5) * (pc + pm);
+                F = T(6) * sigma * kf * pf * (T(1) - pf) * dphi;
+            }
+        }
+        const T beta = T(1) / (T(0.5) * (rho_of(pc, ph) + rho_of(pm, ph)));
+        ku[d] = -adv + beta * visc + beta * F;
+    }
+    (void)h;
+
+    if (write_rhs) {
+        io.rhs_phi[idx] = double(kphi);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) io.rhs_u[d][idx] = double(ku[d]);
+        return;
+    }
+    // ---------------- RK stage update ----------------
+    const T phin = ldg(io.phi_n, idx);
+    if (scheme == 1) {  // forward Euler
+        io.phi_out[idx] = phin + cdt * kphi;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) io.u_out[d][idx] = ldg(io.u_n[d], idx) + cdt * ku[d];
+        return;
+    }
+    if (stage < 3) {
+        T a = stage == 0 ? wdt * kphi : io.acc_phi[idx] + wdt * kphi;
+        io.acc_phi[idx] = a;
+        io.phi_out[idx] = phin + cdt * kphi;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            T au = stage == 0 ? wdt * ku[d] : io.acc_u[d][idx] + wdt * ku[d];
+            io.acc_u[d][idx] = au;
+            io.u_out[d][idx] = ldg(io.u_n[d], idx) + cdt * ku[d];
+        }
+    } else {
+        io.phi_out[idx] = phin + (io.acc_phi[idx] + wdt * kphi);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+            io.u_out[d][idx] = ldg(io.u_n[d], idx) + (io.acc_u[d][idx] + wdt * ku[d]);
+    }
+}
+
+template <typename T, int DIM>
+void launch_stage(const Dims& g, const Phys& ph, const StageIO<T>& io, int stage, int scheme,
+                  double wdt, double cdt, int write_rhs, cudaStream_t s) {
+    k_stage<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(g, ph, io, stage, scheme, T(wdt),
+                                                            T(cdt), write_rhs);
+}
+
+// ---------------------------------------------------------------------------
+// Gamma = gamma_fixed, or max(gamma_min, max |u|)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_gamma(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
+        double gamma_fixed, double gamma_min, double* gamma, RedBuf rb) {
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.ncell; i += gridDim.x * blockDim.x) {
+        m = fmax(m, fabs(double(u0[i])));
+        m = fmax(m, fabs(double(u1[i])));
+        if (DIM == 3) m = fmax(m, fabs(double(u2[i])));
+    }
+    double v[1] = {m}, tot[1];
+    const int mode[1] = {1};
+    if (grid_reduce<1>(v, mode, rb, tot) && threadIdx.x == 0)
+        *gamma = gamma_fixed > 0.0 ? gamma_fixed : fmax(gamma_min, tot[0]);
+}
+
+template <typename T, int DIM>
+void launch_gamma(const Dims& g, const T* const* u, double gamma_fixed, double gamma_min,
+                  double* gamma, RedBuf rb, cudaStream_t s) {
+    k_gamma<T, DIM><<<red_grid(g.ncell), kThreads, 0, s>>>(g, u[0], u[1], DIM == 3 ? u[2] : u[0],
+                                                            gamma_fixed, gamma_min, gamma, rb);
+}
+
+// ---------------------------------------------------------------------------
+// b = D u* / tau (float64) and its sum (the mean is removed by the solver)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
+             double inv_tau, double* __restrict__ b, RedBuf rb, CGScalars* sc) {
+    double s = 0.0;
+    const double inv_h = 1.0 / g.h;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.ncell;
+         idx += gridDim.x * blockDim.x) {
+        Cell c = decode(idx, g);
+        int ip = c.i + 1 == g.nx ? idx - c.i : idx + 1;
+        int jp = c.j + 1 == g.ny ? idx - c.j * g.nx : idx + g.nx;
+        double dv = (double(u0[ip]) - double(u0[idx])) * inv_h;
+        dv += (double(u1[jp]) - double(u1[idx])) * inv_h;
+        if (DIM == 3) {
+            int kp = c.k + 1 == g.nz ? idx - c.k * g.nx * g.ny : idx + g.nx * g.ny;
+            dv += (double(u2[kp]) - double(u2[idx])) * inv_h;
+        }
+        dv *= inv_tau;
+        b[idx] = dv;
+        s += dv;
+    }
+    double v[1] = {s}, tot[1];
+    const int mode[1] = {0};
+    if (grid_reduce<1>(v, mode, rb, tot) && threadIdx.x == 0) sc->mean_b = tot[0] / g.ncell;
+}
+
+template <typename T, int DIM>
+void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double* b, RedBuf rb,
+                       CGScalars* sc, cudaStream_t s) {
+    k_divergence<T, DIM><<<red_grid(g.ncell), kThreads, 0, s>>>(
+        g, u[0], u[1], DIM == 3 ? u[2] : u[0], inv_tau, b, rb, sc);
+}
+
+// ---------------------------------------------------------------------------
+// correction u = u* - tau G p / rho_f
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_correct(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ s0,
+          const T* __restrict__ s1, const T* __restrict__ s2, const double* __restrict__ p,
+          double tau, T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.ncell) return;
+    Cell c = decode(idx, g);
+    const double inv_h = 1.0 / g.h;
+    const T pc = ldg(phi, idx);
+    const double rc = double(rho_of(pc, ph));
+    const double pp = p[idx];
+    int im[3];
+    im[0] = c.i == 0 ? idx + g.nx - 1 : idx - 1;
+    im[1] = c.j == 0 ? idx + (g.ny - 1) * g.nx : idx - g.nx;
+    im[2] = DIM == 3 ? (c.k == 0 ? idx + (g.nz - 1) * g.nx * g.ny : idx - g.nx * g.ny) : idx;
+    const T* sv[3] = {s0, s1, s2};
+    T* ov[3] = {o0, o1, o2};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        double rf = 0.5 * (rc + double(rho_of(ldg(phi, im[d]), ph)));
+        double beta = 1.0 / rf;
+        double gp = (pp - p[im[d]]) * inv_h;
+        ov[d][idx] = T(double(sv[d][idx]) - tau * beta * gp);
+    }
+}
+
+template <typename T, int DIM>
+void launch_correct(const Dims& g, const Phys& ph, const T* phi, const T* const* ustar,
+                    const double* p, double tau, T* const* uout, cudaStream_t s) {
+    k_correct<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(
+        g, ph, phi, ustar[0], ustar[1], DIM == 3 ? ustar[2] : ustar[0], p, tau, uout[0], uout[1],
+        DIM == 3 ? uout[2] : uout[0]);
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics (Section 3.1 Ca_inf, Section 3.2 energies)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_diag(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ u0,
+       const T* __restrict__ u1, const T* __restrict__ u2, const double* __restrict__ p, RedBuf rb,
+       DiagOut* out) {
+    double mass = 0, ke = 0, se = 0, umax = 0, pmin = 1e308, pmax = -1e308;
+    double pin = 0, pout = 0, nin = 0, nout = 0, psum = 0, bad = 0;
+    const double inv_h = 1.0 / g.h, sh = 6.0 * ph.sigma;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.ncell;
+         idx += gridDim.x * blockDim.x) {
+        Cell c = decode(idx, g);
+        double pc = double(phi[idx]);
+        int im[3];
+        im[0] = c.i == 0 ? idx + g.nx - 1 : idx - 1;
+        im[1] = c.j == 0 ? idx + (g.ny - 1) * g.nx : idx - g.nx;
+        im[2] = DIM == 3 ? (c.k == 0 ? idx + (g.nz - 1) * g.nx * g.ny : idx - g.nx * g.ny) : idx;
+        const T* uv[3] = {u0, u1, u2};
+        double rc = double(rho_of(T(pc), ph));
+        double grad2 = 0.0;
+        for (int d = 0; d < DIM; ++d) {
+            double pm = double(phi[im[d]]);
+            double rf = 0.5 * (rc + double(rho_of(T(pm), ph)));
+            double ud = double(uv[d][idx]);
+            ke += 0.5 * rf * ud * ud;
+            umax = fmax(umax, fabs(ud));
+            double df = (pc - pm) * inv_h;
+            grad2 += df * df;
+            if (!isfinite(ud)) bad += 1.0;
+        }
+        double w = pc * (1.0 - pc);
+        se += (sh / ph.eps) * 0.5 * w * w + 0.5 * sh * ph.eps * grad2;
+        mass += pc;
+        pmin = fmin(pmin, pc);
+        pmax = fmax(pmax, pc);
+        double pp = p[idx];
+        psum += pp;
+        if (pc >= 0.999) { pin += pp; nin += 1.0; }
+        if (pc <= 0.001) { pout += pp; nout += 1.0; }
+        if (!isfinite(pc) || !isfinite(pp)) bad += 1.0;
+    }
+    double v[12] = {mass, ke, se, umax, -pmin, pmax, pin, pout, nin, nout, psum, bad};
+    const int mode[12] = {0, 0, 0, 1, 1, 1, 0, 0, 0, 0, 0, 0};
+    double tot[12];
+    if (grid_reduce<12>(v, mode, rb, tot) && threadIdx.x == 0) {
+        double dV = 1.0;
+        for (int d = 0; d < DIM; ++d) dV *= g.h;
+        out->mass = tot[0] * dV;
+        out->ke = tot[1] * dV;
+        out->se = tot[2] * dV;
+        out->umax = tot[3];
+        out->phi_min = -tot[4];
+        out->phi_max = tot[5];
+        out->p_in_sum = tot[6];
+        out->p_out_sum = tot[7];
+        out->n_in = tot[8];
+        out->n_out = tot[9];
+        out->p_sum = tot[10];
+        out->nonfinite = tot[11];
+    }
+}
+
+template <typename T, int DIM>
+void launch_diagnostics(const Dims& g, const Phys& ph, const T* phi, const T* const* u,
+                        const double* p, RedBuf rb, DiagOut* out, cudaStream_t s) {
+    k_diag<T, DIM><<<red_grid(g.ncell), kThreads, 0, s>>>(g, ph, phi, u[0], u[1],
+                                                           DIM == 3 ? u[2] : u[0], p, rb, out);
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+#define PF_INST_TD(T, D)                                                                        \
+    template void launch_init_phi<T, D>(const Dims&, const Phys&, double, int, double, T*,      \
+                                        cudaStream_t);                                          \
+    template void launch_cell_pass<T, D>(const Dims&, const Phys&, const T*, T*, T*, T*, T*,    \
+                                         cudaStream_t);                                         \
+    template void launch_stage<T, D>(const Dims&, const Phys&, const StageIO<T>&, int, int,     \
+                                     double, double, int, cudaStream_t);                        \
+    template void launch_gamma<T, D>(const Dims&, const T* const*, double, double, double*,     \
+                                     RedBuf, cudaStream_t);                                     \
+    template void launch_divergence<T, D>(const Dims&, const T* const*, double, double*,        \
+                                          RedBuf, CGScalars*, cudaStream_t);                    \
+    template void launch_correct<T, D>(const Dims&, const Phys&, const T*, const T* const*,     \
+                                       const double*, double, T* const*, cudaStream_t);         \
+    template void launch_diagnostics<T, D>(const Dims&, const Phys&, const T*, const T* const*, \
+                                           const double*, RedBuf, DiagOut*, cudaStream_t);
+
+PF_INST_TD(double, 2)
+PF_INST_TD(double, 3)
+PF_INST_TD(float, 2)
+PF_INST_TD(float, 3)
+
+template void launch_convert_in<double>(const double*, double*, int, cudaStream_t);
+template void launch_convert_in<float>(const double*, float*, int, cudaStream_t);
+template void launch_convert_out<double>(const double*, double*, int, double, const double*,
+                                         double, cudaStream_t);
+template void launch_convert_out<float>(const float*, double*, int, double, const double*, double,
+                                        cudaStream_t);
+
+}  // namespace pf

@@ -1,0 +1,84 @@
+"""The C-ABI library loads, exports every entry point include/pf.h declares,
+and its host-side validation works (no GPU needed: no compute call is made)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2205_05835_gb300 as pf
+
+    return pf
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pf.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:pf_status|void|size_t|int|const char\*)\s+(pf_\w+)\s*\(",
+                                 src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("pf_init", "pf_step", "pf_project", "pf_diagnostics", "pf_workspace_size",
+              "pf_destroy", "pf_last_error", "pf_get_state", "pf_set_state"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(pf):
+    import ctypes
+
+    lib = ctypes.CDLL(pf.B.LIB_PATH)
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+    assert set(declared_symbols()) == set(pf.B.SYMBOLS)
+
+
+def test_workspace_size_and_validation(pf):
+    import pf_inputs as I
+
+    p = pf.make_params(I.static_drop_64())
+    n64 = pf.pf_workspace_size(p)
+    assert n64 > 64 * 64 * 8 * 10
+    p2 = pf.make_params(I.oscillating_drop_384(n=64))
+    assert pf.pf_workspace_size(p2) > 64 ** 3 * 4 * 20
+    # mixed precision needs fewer bytes than fp64 for the same grid
+    pm = pf.make_params(dict(I.oscillating_drop_384(n=64), precision="fp64"))
+    assert pf.pf_workspace_size(pm) > pf.pf_workspace_size(p2)
+    bad = pf.make_params(I.static_drop_64())
+    bad.dim = 4
+    with pytest.raises(pf.PFError) as e:
+        pf.pf_workspace_size(bad)
+    assert e.value.status == pf.B.PF_ERR_INVALID
+    bad = pf.make_params(I.static_drop_64())
+    bad.n[0] = 2
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(bad)
+    bad = pf.make_params(I.static_drop_64())
+    bad.dt = 0.0
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(bad)
+    bad = pf.make_params(I.static_drop_64())
+    bad.reserved[3] = 1
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(bad)
+
+
+def test_init_rejects_bad_workspace_without_touching_the_gpu(pf):
+    import ctypes
+
+    import pf_inputs as I
+
+    p = pf.make_params(I.static_drop_64())
+    ctx = ctypes.c_void_p(0)
+    st = pf.B.LIB.pf_init(ctypes.byref(p), None, 0, None, None, ctypes.byref(ctx))
+    assert st == pf.B.PF_ERR_WORKSPACE
+    assert "workspace" in pf.pf_last_error(None)
+    st = pf.B.LIB.pf_init(ctypes.byref(p), 0x1001, 1 << 40, None, None, ctypes.byref(ctx))
+    assert st == pf.B.PF_ERR_WORKSPACE

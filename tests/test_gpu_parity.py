@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Float64 path: fields within 1e-10 relative (max |gpu - oracle| / max |oracle|)
+of the oracle; the CG solves are run to a relative residual the oracle's exact
+solve can be compared with. Mixed path: per-field bounds stated in each test.
+"""
+import numpy as np
+import pytest
+
+import pf_inputs as I
+from oracle import pf_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2205_05835_gb300 as pf
+
+    return pf
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def rand_velocity(g, seed, amp=0.3):
+    """Seeded face velocity (not divergence free) for operator tests."""
+    return [amp * (I.noise(g.shape, seed + d) - 0.5) for d in range(g.dim)]
+
+
+# --------------------------------------------------------------------------
+# initial condition
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n,mode", [(2, 40, 2), (2, 33, 0), (3, 24, 2), (3, 20, 3)])
+def test_init_profile(pf, dim, n, mode):
+    p = I.small_case(dim=dim, n=n, pert_mode=mode, pert_amp=0.05 if mode else 0.0)
+    sim = pf.Simulation(p)
+    want = O.initial_phi(O.params_from(p))
+    assert np.max(np.abs(sim.field("phi") - want)) < 1e-14
+    for c in "uvw"[:dim]:
+        assert np.max(np.abs(sim.field(c))) == 0.0
+    sim.close()
+
+
+# --------------------------------------------------------------------------
+# operator parity: phase-field and momentum right-hand sides
+# --------------------------------------------------------------------------
+CASES = [(m, f) for m in ("cdi", "sb", "isodi") for f in ("eb", "csf", "lcsf")]
+
+
+@pytest.mark.parametrize("model,force", CASES)
+@pytest.mark.parametrize("dim,n", [(2, (40, 40, 1)), (3, (24, 20, 16))])
+def test_rhs_parity_fp64(pf, model, force, dim, n):
+    p = I.small_case(dim=dim, n=n[0], model=model, force=force)
+    p["n"] = n
+    po = O.params_from(p)
+    g = O.Grid(dim, n, p["L"])
+    phi = O.initial_phi(po) + 0.02 * (I.noise(g.shape, 7) - 0.5)
+    u = rand_velocity(g, 11)
+    sim = pf.Simulation(p, phi0=phi)
+    for d in range(dim):
+        sim.set_field("uvw"[d], u[d])
+    gam = 0.37
+    kphi, ku = sim.eval_rhs(gam)
+    want_phi = O.phase_rhs(phi, u, g, po, gam)
+    want_u = O.momentum_rhs(phi, u, g, po)
+    assert rel(kphi, want_phi) < 1e-12
+    for d in range(dim):
+        assert rel(ku[d], want_u[d]) < 1e-12, d
+    sim.close()
+
+
+@pytest.mark.parametrize("model,force", [("cdi", "eb"), ("isodi", "lcsf"), ("sb", "csf")])
+def test_rhs_parity_mixed(pf, model, force):
+    """float32 stencils: relative to the field scale, within 2e-5 (phase field) and
+    1e-4 (momentum, where the force is a difference of O(1/eps) terms)."""
+    p = I.small_case(dim=3, n=24, model=model, force=force, precision="mixed")
+    po = O.params_from(p)
+    g = O.Grid(3, p["n"], p["L"])
+    phi = O.initial_phi(po)
+    u = rand_velocity(g, 3, amp=0.1)
+    sim = pf.Simulation(p, phi0=phi)
+    for d in range(3):
+        sim.set_field("uvw"[d], u[d])
+    # the mixed path stores phi and u in float32: compare with the oracle on the
+    # rounded inputs
+    phi32 = phi.astype(np.float32).astype(np.float64)
+    u32 = [c.astype(np.float32).astype(np.float64) for c in u]
+    kphi, ku = sim.eval_rhs(0.2)
+    assert rel(kphi, O.phase_rhs(phi32, u32, g, po, 0.2)) < 2e-5
+    want_u = O.momentum_rhs(phi32, u32, g, po)
+    for d in range(3):
+        assert rel(ku[d], want_u[d]) < 1e-4
+    sim.close()
+
+
+# --------------------------------------------------------------------------
+# Poisson solve
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n,ratio", [(2, (48, 48, 1), 1000.0), (2, (40, 40, 1), 10.0),
+                                         (3, (16, 16, 16), 100.0), (3, (24, 20, 16), 10.0)])
+def test_poisson_solve_fp64(pf, dim, n, ratio):
+    p = I.small_case(dim=dim, n=n[0], rho_in=ratio, rho_out=1.0, poisson_rtol=1e-13,
+                     poisson_maxit=400)
+    p["n"] = n
+    po = O.params_from(p)
+    g = O.Grid(dim, n, p["L"])
+    phi = O.initial_phi(po)
+    rhs = I.noise(g.shape, 5) - 0.5
+    rhs -= rhs.mean()
+    sim = pf.Simulation(p, phi0=phi)
+    x, it, relres, st = sim.poisson_solve(rhs)
+    assert st == 0, pf.pf_last_error(sim.ctx)
+    assert relres <= 1e-13
+    beta = O.face_beta(phi, g, po)
+    want = O.solve_poisson(beta, rhs, g)
+    assert rel(x, want) < 1e-9
+    res = O.apply_poisson(beta, x, g) - rhs
+    assert np.linalg.norm(res) <= 2e-13 * np.linalg.norm(rhs)
+    sim.close()
+
+
+def test_poisson_mixed_preconditioner_reaches_fp64_residual(pf):
+    """float32 V-cycles inside the float64 CG still reach a 1e-12 float64 residual."""
+    p = I.small_case(dim=3, n=32, rho_in=10.0, rho_out=1.0, precision="mixed",
+                     poisson_rtol=1e-12, poisson_maxit=200)
+    po = O.params_from(p)
+    g = O.Grid(3, p["n"], p["L"])
+    phi = O.initial_phi(po)
+    rhs = I.noise(g.shape, 9) - 0.5
+    rhs -= rhs.mean()
+    sim = pf.Simulation(p, phi0=phi)
+    x, it, relres, st = sim.poisson_solve(rhs)
+    assert st == 0 and relres <= 1e-12
+    phi32 = phi.astype(np.float32).astype(np.float64)
+    beta = O.face_beta(phi32, g, po)
+    res = O.apply_poisson(beta, x, g) - rhs
+    assert np.linalg.norm(res) <= 2e-12 * np.linalg.norm(rhs)
+    sim.close()
+
+
+def test_poisson_iteration_cap_reports_not_converged(pf):
+    p = I.small_case(dim=2, n=32, poisson_rtol=1e-14, poisson_maxit=1)
+    po = O.params_from(p)
+    g = O.Grid(2, p["n"], p["L"])
+    sim = pf.Simulation(p)
+    rhs = I.noise(g.shape, 1) - 0.5
+    x, it, relres, st = sim.poisson_solve(rhs - rhs.mean())
+    assert st == pf.B.PF_ERR_NOT_CONVERGED and it == 1
+    # the context stays usable
+    sim2 = pf.Simulation(dict(p, poisson_maxit=200))
+    x, it, relres, st = sim2.poisson_solve(rhs - rhs.mean())
+    assert st == 0
+    sim.close()
+    sim2.close()
+
+
+# --------------------------------------------------------------------------
+# whole steps
+# --------------------------------------------------------------------------
+def run_both(pf, p, steps):
+    po = O.params_from(p)
+    phi0 = O.initial_phi(po)
+    sim = pf.Simulation(p, phi0=phi0)
+    sim.step(steps)
+    st = O.run(po, steps=steps, phi0=phi0)
+    return sim, st
+
+
+@pytest.mark.parametrize("model,force,scheme", [
+    ("cdi", "eb", "rk4"), ("cdi", "csf", "rk4"), ("cdi", "lcsf", "rk4"),
+    ("sb", "eb", "rk4"), ("isodi", "eb", "fe"), ("sb", "lcsf", "fe")])
+def test_step_parity_fp64_2d(pf, model, force, scheme):
+    p = I.small_case(dim=2, n=40, model=model, force=force, scheme=scheme,
+                     poisson_rtol=1e-13, poisson_maxit=300, gamma_min=0.05)
+    sim, st = run_both(pf, p, 5)
+    assert rel(sim.field("phi"), st.phi) < TOL64
+    assert rel(sim.field("u"), st.u[0]) < TOL64
+    assert rel(sim.field("v"), st.u[1]) < TOL64
+    assert rel(sim.field("p"), st.p) < TOL64
+    d = sim.diagnostics()
+    od = O.diagnostics(st, p)
+    for k in ("mass", "ke", "se", "umax", "phi_min", "phi_max", "dp_laplace"):
+        assert abs(d[k] - od[k]) <= 1e-10 * max(abs(od[k]), 1e-30) + 1e-300, k
+    sim.close()
+
+
+@pytest.mark.parametrize("force", ["eb", "lcsf"])
+def test_step_parity_fp64_3d(pf, force):
+    p = I.small_case(dim=3, n=16, force=force, poisson_rtol=1e-13, poisson_maxit=300)
+    p["n"] = (16, 16, 16)
+    sim, st = run_both(pf, p, 3)
+    for name, ref in (("phi", st.phi), ("u", st.u[0]), ("v", st.u[1]), ("w", st.u[2]),
+                      ("p", st.p)):
+        assert rel(sim.field(name), ref) < TOL64, name
+    sim.close()
+
+
+def test_static_drop_64_fp64_200_steps(pf):
+    """The 64^2 static drop (FP64, CDI + EB, La = 12000) over its 200 steps."""
+    p = dict(I.static_drop_64(), poisson_rtol=1e-13, poisson_maxit=300)
+    sim, st = run_both(pf, p, p["steps"])
+    for name, ref in (("phi", st.phi), ("u", st.u[0]), ("v", st.u[1]), ("p", st.p)):
+        assert rel(sim.field(name), ref) < TOL64, name
+    d = sim.diagnostics()
+    od = O.diagnostics(st, p)
+    assert abs(d["ca_inf"] - od["ca_inf"]) <= 1e-10 * od["ca_inf"]
+    assert abs(d["mass"] - od["mass"]) <= 1e-13 * od["mass"]
+    assert d["poisson_relres"] <= 1e-13
+    sim.close()
+
+
+def test_step_mixed_per_field_error(pf):
+    """Mixed precision vs the FP64 oracle after 5 RK4 steps (ratio-10 drop):
+    phi within 1e-5, velocity within 2e-3 of its max, pressure within 1e-4."""
+    p = I.small_case(dim=2, n=48, precision="mixed", poisson_rtol=1e-12)
+    po = O.params_from(p)
+    phi0 = O.initial_phi(po).astype(np.float32).astype(np.float64)
+    sim = pf.Simulation(p, phi0=phi0)
+    sim.step(5)
+    st = O.run(dict(po, precision="fp64"), steps=5, phi0=phi0)
+    assert rel(sim.field("phi"), st.phi) < 1e-5
+    assert rel(sim.field("u"), st.u[0]) < 2e-3
+    assert rel(sim.field("v"), st.u[1]) < 2e-3
+    assert rel(sim.field("p"), st.p) < 1e-4
+    sim.close()
+
+
+def test_state_round_trip_and_restart(pf):
+    """get_state / set_state restarts bit-identically (checkpoint/resume)."""
+    p = I.small_case(dim=2, n=32, poisson_rtol=1e-13)
+    a = pf.Simulation(p)
+    a.step(2)
+    buf = np.empty(a.state_bytes(), dtype=np.uint8)
+    pf.pf_get_state(a.ctx, buf.ctypes.data)
+    a.step(2)
+    b = pf.Simulation(p)
+    pf.pf_set_state(b.ctx, buf.ctypes.data)
+    b.step(2)
+    for name in ("phi", "u", "v", "p"):
+        np.testing.assert_array_equal(a.field(name), b.field(name))
+    assert a.diagnostics()["step"] == b.diagnostics()["step"] == 4
+    a.close()
+    b.close()
+
+
+def test_nonfinite_input_is_reported(pf):
+    p = I.small_case(dim=2, n=32)
+    po = O.params_from(p)
+    phi = O.initial_phi(po)
+    phi[3, 5] = np.nan
+    sim = pf.Simulation(p, phi0=phi)
+    with pytest.raises(pf.PFError) as e:
+        sim.diagnostics()
+    assert e.value.status == pf.B.PF_ERR_NONFINITE
+    sim.close()
+
+
+@pytest.mark.parametrize("n", [(4, 4, 1), (6, 10, 1), (4, 4, 4), (12, 8, 6)])
+def test_tiny_and_odd_grids(pf, n):
+    dim = 2 if n[2] == 1 else 3
+    p = I.small_case(dim=dim, n=n[0], poisson_rtol=1e-13, poisson_maxit=500, R=0.3)
+    p["n"] = n
+    sim, st = run_both(pf, p, 2)
+    assert rel(sim.field("phi"), st.phi) < TOL64
+    assert rel(sim.field("p"), st.p) < 1e-9
+    sim.close()

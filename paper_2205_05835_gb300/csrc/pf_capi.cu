@@ -34,8 +34,8 @@ struct Carver {
 
 const char* kClassNames[KC_COUNT] = {
     "cell_pass", "stage", "gamma", "divergence", "correct", "mg_coarsen_beta", "mg_gs_level0",
-    "mg_gs_coarse_levels", "mg_restrict", "mg_prolong", "mg_coarse_vcycle", "cg_start", "cg_dots",
-    "cg_dir_spmv", "cg_update", "diagnostics", "misc"};
+    "mg_gs_coarse_levels", "mg_restrict", "mg_prolong", "mg_coarse_vcycle", "ir_residual_f64",
+    "cg_dots", "cg_dir_spmv", "cg_update", "diagnostics", "misc", "ir_addcorr", "beta0_f64"};
 
 const double kRK4C[4] = {0.0, 0.5, 0.5, 1.0};
 const double kRK4W[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
@@ -159,8 +159,9 @@ struct ImplT final : Impl {
     T *phiN, *phiA, *phiB, *accphi;
     T *uN[3], *uS[3], *uStar[3], *accu[3];
     T *nrm[3], *aux;
-    double *p, *b, *r, *pd[2], *q;
-    T *rT, *z;
+    double *p, *b;
+    double* beta64[3];   // float64 face coefficients (float64 path only)
+    T *rT, *z, *pd[2], *qT, *eT;
     MGHier<T> H;
     RedBuf rb;
     CGScalars* sc;
@@ -247,19 +248,18 @@ struct ImplT final : Impl {
         aux = cv.take<T>(2 * n);
         p = cv.take<double>(n);
         b = cv.take<double>(n);
-        r = cv.take<double>(n);
-        pd[0] = cv.take<double>(n);
-        pd[1] = cv.take<double>(n);
-        q = cv.take<double>(n);
-        if (sizeof(T) == sizeof(double)) {
-            rT = reinterpret_cast<T*>(r);
-        } else {
-            rT = cv.take<T>(n);
-        }
+        rT = cv.take<T>(n);
         z = cv.take<T>(n);
+        pd[0] = cv.take<T>(n);
+        pd[1] = cv.take<T>(n);
+        qT = cv.take<T>(n);
+        eT = cv.take<T>(n);
+        for (int d = 0; d < 3; ++d)
+            beta64[d] = (sizeof(T) == sizeof(double) && d < DIM) ? cv.take<double>(n) : nullptr;
         H.lev[0].x = z;
         H.lev[0].f = rT;
-        for (int d = 0; d < 3; ++d) H.lev[0].beta[d] = nullptr;
+        for (int d = 0; d < 3; ++d)
+            H.lev[0].beta[d] = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(beta64[d]) : nullptr;
         for (int l = 1; l < H.nlev; ++l) {
             const size_t m = H.lev[l].g.ncell;
             H.lev[l].x = cv.take<T>(m);
@@ -291,15 +291,19 @@ struct ImplT final : Impl {
             CK(cudaMemsetAsync(accu[d], 0, n * sizeof(T), st));
         }
         CK(cudaMemsetAsync(p, 0, n * sizeof(double), st));
-        CK(cudaMemsetAsync(q, 0, n * sizeof(double), st));
-        CK(cudaMemsetAsync(pd[0], 0, n * sizeof(double), st));
-        CK(cudaMemsetAsync(pd[1], 0, n * sizeof(double), st));
+        CK(cudaMemsetAsync(qT, 0, n * sizeof(T), st));
+        CK(cudaMemsetAsync(pd[0], 0, n * sizeof(T), st));
+        CK(cudaMemsetAsync(pd[1], 0, n * sizeof(T), st));
+        CK(cudaMemsetAsync(eT, 0, n * sizeof(T), st));
         CK(cudaMemsetAsync(aux, 0, 2 * n * sizeof(T), st));
         CK(cudaMemsetAsync(rb.counter, 0, 4 * sizeof(unsigned int), st));
         CGScalars s0;
         memset(&s0, 0, sizeof(s0));
         s0.rtol2 = prm.poisson_rtol * prm.poisson_rtol;
         s0.maxit = prm.poisson_maxit;
+        // inner relative tolerance floor: float32 inner solves gain ~4 digits per
+        // outer step; float64 inner solves go straight to the final tolerance
+        s0.eta2_min = sizeof(T) == sizeof(double) ? 0.0 : 1e-8;
         *h_sc = s0;
         CK(cudaMemcpyAsync(sc, h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(gamma, 0, sizeof(double), st));
@@ -329,50 +333,90 @@ struct ImplT final : Impl {
         pf_status s = solve(phi, -1.0);
         if (s != PF_OK) return s;
         prof.begin(KC_CORRECT);
-        launch_correct<T, DIM>(g, ph, phi, uin_c, p, tau, uout, st);
+        launch_correct<T, DIM>(g, ph, phi, sizeof(T) == sizeof(double) ? beta64 : nullptr, uin_c,
+                               p, tau, uout, st);
         prof.end();
         return PF_OK;
     }
 
-    // CG on A p = sign (b - mean b), warm start from p
+    SolveIO<T, DIM> solve_io(const T* phi, double sign) {
+        SolveIO<T, DIM> io;
+        io.phi = phi;
+        for (int d = 0; d < 3; ++d) io.beta64[d] = sizeof(T) == sizeof(double) ? beta64[d] : nullptr;
+        io.b = b;
+        io.sign = sign;
+        io.x = p;
+        io.r = rT;
+        io.z = z;
+        io.p[0] = pd[0];
+        io.p[1] = pd[1];
+        io.q = qT;
+        io.e = eT;
+        return io;
+    }
+
+    pf_status poll() {
+        CK(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        prof.harvest();
+        return PF_OK;
+    }
+
+    // A x = sign (b - mean b): float64 iterative refinement around inner
+    // MG-preconditioned CG in T, warm start from x = p
     pf_status solve(const T* phi, double sign) {
+        const SolveIO<T, DIM> io = solve_io(phi, sign);
+        if (sizeof(T) == sizeof(double)) {
+            prof.begin(KC_BETA0);
+            launch_beta0<T, DIM>(g, ph, phi, beta64, st);
+            prof.end();
+        }
         prof.begin(KC_COARSEN);
         launch_mg_setup<T, DIM>(g, ph, phi, H, st);
         prof.end();
-        prof.begin(KC_CG_START);
-        launch_cg_start<T, DIM>(g, ph, phi, b, sign, p, r, rT, rb, sc, st);
+        prof.begin(KC_IR_RESIDUAL);
+        launch_ir_residual<T, DIM>(g, ph, io, 1, rb, sc, st);
         prof.end();
-        int cur = 0;
-        const int maxit = prm.poisson_maxit;
-        int it = 0;
-        int poll = 1;
-        while (it < maxit) {
-            const int first = (it == 0);
-            launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof);
-            prof.begin(KC_CG_DOTS);
-            launch_cg_dots<T, DIM>(g, z, r, q, first, rb, sc, st);
-            prof.end();
-            prof.begin(KC_CG_DIR);
-            launch_cg_dir<T, DIM>(g, ph, phi, z, pd[cur], pd[1 - cur], q, first, rb, sc, st);
-            prof.end();
-            prof.begin(KC_CG_UPDATE);
-            launch_cg_update<T, DIM>(g, pd[1 - cur], q, p, r, rT, rb, sc, st);
-            prof.end();
-            cur = 1 - cur;
-            ++it;
-            if (it % poll == 0 || it == maxit) {
-                CK(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                prof.harvest();
-                if (h_sc->done) break;
+        pf_status ps = poll();
+        if (ps != PF_OK) return ps;
+        const int poll_every = 2;
+        int outer = 0;
+        while (!h_sc->done && outer < 64) {
+            int cur = 0;
+            for (int it = 0; it <= prm.poisson_maxit + poll_every; ++it) {
+                const int first = (it == 0);
+                launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof);
+                prof.begin(KC_CG_DOTS);
+                launch_in_dots<T, DIM>(g, io, first, rb, sc, st);
+                prof.end();
+                prof.begin(KC_CG_DIR);
+                launch_in_dir<T, DIM>(g, ph, io, cur, first, rb, sc, st);
+                prof.end();
+                prof.begin(KC_CG_UPDATE);
+                launch_in_update<T, DIM>(g, io, cur, first, rb, sc, st);
+                prof.end();
+                cur = 1 - cur;
+                if ((it + 1) % poll_every == 0) {
+                    ps = poll();
+                    if (ps != PF_OK) return ps;
+                    if (h_sc->idone || h_sc->done) break;
+                }
             }
+            prof.begin(KC_IR_ADDCORR);
+            launch_ir_addcorr<T, DIM>(g, io, sc, st);
+            prof.end();
+            prof.begin(KC_IR_RESIDUAL);
+            launch_ir_residual<T, DIM>(g, ph, io, 0, rb, sc, st);
+            prof.end();
+            ps = poll();
+            if (ps != PF_OK) return ps;
+            ++outer;
         }
-        CK(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
         last_iters = h_sc->iters;
         if (last_iters > max_iters) max_iters = last_iters;
         last_relres = h_sc->ff > 0 ? sqrt(h_sc->rr / h_sc->ff) : 0.0;
+        if (!h_sc->done && h_sc->status == 0) h_sc->status = PF_ERR_NOT_CONVERGED;
         if (h_sc->status) {
             int stt = h_sc->status;
             h_sc->status = 0;
@@ -601,17 +645,19 @@ struct ImplT final : Impl {
             io.u_out[d] = uStar[d];
             io.nrm[d] = nrm[d];
         }
-        // outputs staged in float64 device buffers: kphi -> b, ku -> pd[0], pd[1], q
-        io.rhs_phi = b;
-        io.rhs_u[0] = pd[0];
-        io.rhs_u[1] = pd[1];
-        io.rhs_u[2] = q;
+        // outputs in scratch arrays of the storage type (phiA, u*), then
+        // converted to float64 one field at a time through b
+        io.rhs_phi = phiA;
+        for (int d = 0; d < 3; ++d) io.rhs_u[d] = uStar[d];
         launch_cell_pass<T, DIM>(g, ph, phiN, nrm[0], nrm[1], nrm[2], aux, st);
         launch_stage<T, DIM>(g, ph, io, 0, 0, 0.0, 0.0, 1, st);
         const size_t bytes = (size_t)g.ncell * sizeof(double);
+        launch_convert_out<T>(phiA, b, g.ncell, 0.0, nullptr, 0.0, st);
         CK(cudaMemcpyAsync(kphi, b, bytes, cudaMemcpyDefault, st));
-        for (int d = 0; d < DIM; ++d)
-            CK(cudaMemcpyAsync(ku + (size_t)d * g.ncell, io.rhs_u[d], bytes, cudaMemcpyDefault, st));
+        for (int d = 0; d < DIM; ++d) {
+            launch_convert_out<T>(uStar[d], b, g.ncell, 0.0, nullptr, 0.0, st);
+            CK(cudaMemcpyAsync(ku + (size_t)d * g.ncell, b, bytes, cudaMemcpyDefault, st));
+        }
         CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
         return PF_OK;

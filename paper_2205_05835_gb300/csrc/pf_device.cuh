@@ -54,6 +54,100 @@ struct Nbr {
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p, int i) { return __ldg(p + i); }
 
+// Density (linear in clip(phi, 0, 1), phi = 1 the drop).
+template <typename T>
+__device__ __forceinline__ T rho_of_p(T phi, const Phys& ph) {
+    T c = phi < T(0) ? T(0) : (phi > T(1) ? T(1) : phi);
+    return T(ph.rho_out) + (T(ph.rho_in) - T(ph.rho_out)) * c;
+}
+
+// 1 / rho_f of the face between two cells in float32: a correctly rounded
+// reciprocal, used identically by the pressure operator, the smoother and the
+// velocity correction of the mixed-precision path.
+// Written with explicitly rounded operations (no contraction into FMA) so the
+// operator is reproducible bit for bit by any IEEE float32 evaluation.
+__device__ __forceinline__ float rho32(float phi, const Phys& ph) {
+    const float c = phi < 0.f ? 0.f : (phi > 1.f ? 1.f : phi);
+    const float ro = float(ph.rho_out), dr = __fsub_rn(float(ph.rho_in), float(ph.rho_out));
+    return __fadd_rn(ro, __fmul_rn(dr, c));
+}
+__device__ __forceinline__ float beta_face32(float pa, float pb, const Phys& ph) {
+    return __frcp_rn(__fmul_rn(0.5f, __fadd_rn(rho32(pa, ph), rho32(pb, ph))));
+}
+
+// a / b: IEEE division in float64, multiplication by the correctly rounded
+// reciprocal in float32.
+__device__ __forceinline__ double divq(double a, double b) { return a / b; }
+__device__ __forceinline__ float divq(float a, float b) { return a * __frcp_rn(b); }
+
+// Row-wise cell loop: a block covers whole rows of nx cells (x fastest), so
+// (i, j, k) need no per-cell division; rows are strided by the grid. Threads
+// beyond the last full row of the block do nothing (but still reach any
+// reduction that follows).
+template <typename F>
+__device__ __forceinline__ void for_cells(const Dims& g, F f) {
+    const int nxe = g.nx < (int)blockDim.x ? g.nx : (int)blockDim.x;
+    const int rpb = blockDim.x / nxe;
+    const int rsub = threadIdx.x / nxe;
+    if (rsub >= rpb) return;
+    const int i0 = threadIdx.x - rsub * nxe;
+    const int nrows = g.ny * g.nz;
+    for (int row = blockIdx.x * rpb + rsub; row < nrows; row += gridDim.x * rpb) {
+        const int k = row / g.ny, j = row - k * g.ny;
+        const int base = row * g.nx;
+        for (int i = i0; i < g.nx; i += nxe) f(i, j, k, base + i);
+    }
+}
+
+// Same, over the cells of one colour ((i + j + k) % 2 == color).
+template <typename F>
+__device__ __forceinline__ void for_color_cells(const Dims& g, int color, F f) {
+    const int nh = (g.nx + 1) >> 1;
+    const int nxe = nh < (int)blockDim.x ? nh : (int)blockDim.x;
+    const int rpb = blockDim.x / nxe;
+    const int rsub = threadIdx.x / nxe;
+    if (rsub >= rpb) return;
+    const int m0 = threadIdx.x - rsub * nxe;
+    const int nrows = g.ny * g.nz;
+    for (int row = blockIdx.x * rpb + rsub; row < nrows; row += gridDim.x * rpb) {
+        const int k = row / g.ny, j = row - k * g.ny;
+        const int base = row * g.nx;
+        const int s = (j + k + color) & 1;
+        for (int i = 2 * m0 + s; i < g.nx; i += 2 * nxe) f(i, j, k, base + i);
+    }
+}
+
+// Periodic neighbour indices (-x, +x, -y, +y, -z, +z) of cell (i, j, k).
+struct Nb6 {
+    int m[6];
+};
+template <int DIM>
+__device__ __forceinline__ Nb6 nb6(const Dims& g, int i, int j, int k, int idx) {
+    Nb6 n;
+    const int sxy = g.nx * g.ny;
+    n.m[0] = i == 0 ? idx + g.nx - 1 : idx - 1;
+    n.m[1] = i == g.nx - 1 ? idx - (g.nx - 1) : idx + 1;
+    n.m[2] = j == 0 ? idx + (g.ny - 1) * g.nx : idx - g.nx;
+    n.m[3] = j == g.ny - 1 ? idx - (g.ny - 1) * g.nx : idx + g.nx;
+    if (DIM == 3) {
+        n.m[4] = k == 0 ? idx + (g.nz - 1) * sxy : idx - sxy;
+        n.m[5] = k == g.nz - 1 ? idx - (g.nz - 1) * sxy : idx + sxy;
+    } else {
+        n.m[4] = n.m[5] = idx;
+    }
+    return n;
+}
+
+// Grid size of a row-wise kernel (cap: fixed grid of reduction kernels).
+inline int row_grid(const Dims& g, int threads, int cap) {
+    int nxe = g.nx < threads ? g.nx : threads;
+    int rpb = threads / nxe;
+    long long rows = (long long)g.ny * g.nz;
+    long long b = (rows + rpb - 1) / rpb;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
 // Sum of K values over the block (deterministic order). Result valid in thread 0.
 template <int K>
 __device__ __forceinline__ void block_reduce_sum(double (&v)[K], double* smem /* K*32 */) {

@@ -39,27 +39,33 @@ struct StageIO {
     const T* nrm[3];     // cell normals of phi_s (scratch)
     const T* aux;        // mu (EB) or kappa (CSF/LCSF/SB/ISODI) of phi_s (scratch)
     const double* gamma; // device scalar
-    double* rhs_phi;     // float64 right-hand sides (operator evaluation only)
-    double* rhs_u[3];
+    T* rhs_phi;          // right-hand sides (operator evaluation only)
+    T* rhs_u[3];
 };
 
-// Scalars of one conjugate-gradient solve kept on the device. Reductions
-// write them from the last block of each kernel; no host round trip.
+// Scalars of one pressure solve kept on the device. The solve is iterative
+// refinement: a float64 outer residual r = f - A x and inner preconditioned CG
+// in the storage precision T on A e = r (T = double: the inner CG is the whole
+// solve). Reductions write these from the last block of each kernel; the host
+// only polls `done` / `idone`.
 struct CGScalars {
     double ff;        // ||f||^2 of the right-hand side
-    double rr;        // ||r||^2
-    double rz;        // r.z (current)
-    double rz_old;
-    double zq;        // z.q (flexible beta)
-    double pq;        // p.q
-    double alpha, beta;
-    double mean_b;    // mean of the divergence (removed)
-    double sum_x;
-    double rtol2;     // squared relative tolerance (set at init)
-    int maxit;        // iteration cap (set at init)
-    int done;         // 1 once converged or stopped (kernels early-exit)
-    int iters;        // iterations of the current / last solve
+    double rr;        // ||f - A x||^2 (float64, true residual)
+    double rr0_in;    // ||r_in||^2 at the start of the inner solve
+    double rr_in;     // ||r_in||^2 (recursive inner residual)
+    double rz, zq, pq, alpha, beta;
+    double mean_b;    // mean of the right-hand side (removed)
+    double rtol2;     // squared relative tolerance of the solve (set at init)
+    double eta2_min;  // squared floor of the inner relative tolerance
+    double eta2;      // squared inner relative tolerance of the current outer step
+    int maxit;        // cap on inner iterations per solve (set at init)
+    int done;         // 1 once converged or stopped (all kernels early-exit)
+    int idone;        // 1 once the inner solve stopped (inner kernels early-exit)
+    int iters;        // inner iterations of the current / last solve
+    int outer;        // outer residual evaluations of the current / last solve
     int status;       // latched device error (pf_status value), 0 if none
+    int capped;       // inner iteration cap reached
+    int pad;
 };
 
 // One multigrid level of the preconditioner.
@@ -95,8 +101,8 @@ struct DiagOut {
 // Kernel classes timed by the optional profiler.
 enum KernelClass {
     KC_CELL = 0, KC_STAGE, KC_GAMMA, KC_DIV, KC_CORRECT, KC_COARSEN, KC_GS0, KC_GS,
-    KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_CG_START, KC_CG_DOTS, KC_CG_DIR, KC_CG_UPDATE,
-    KC_DIAG, KC_MISC, KC_COUNT
+    KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_IR_RESIDUAL, KC_CG_DOTS, KC_CG_DIR, KC_CG_UPDATE,
+    KC_DIAG, KC_MISC, KC_IR_ADDCORR, KC_BETA0, KC_COUNT
 };
 
 // Launch counter and optional CUDA-event timer per kernel class. Event pairs
@@ -137,8 +143,9 @@ template <typename T, int DIM>
 void launch_gamma(const Dims& g, const T* const* u, double gamma_fixed, double gamma_min,
                   double* gamma, RedBuf rb, cudaStream_t s);
 template <typename T, int DIM>
-void launch_correct(const Dims& g, const Phys& ph, const T* phi, const T* const* ustar,
-                    const double* p, double tau, T* const* uout, cudaStream_t s);
+void launch_correct(const Dims& g, const Phys& ph, const T* phi, const double* const* beta64,
+                    const T* const* ustar, const double* p, double tau, T* const* uout,
+                    cudaStream_t s);
 template <typename T, int DIM>
 void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double* b, RedBuf rb,
                        CGScalars* sc, cudaStream_t s);
@@ -146,25 +153,44 @@ template <typename T, int DIM>
 void launch_diagnostics(const Dims& g, const Phys& ph, const T* phi, const T* const* u,
                         const double* p, RedBuf rb, DiagOut* out, cudaStream_t s);
 
-// Poisson (MG-preconditioned flexible CG, float64 outer iteration)
+// Poisson: float64 iterative refinement around multigrid-preconditioned
+// flexible CG in precision T.
+template <typename T, int DIM>
+struct SolveIO {
+    const T* phi;          // phase field defining rho
+    const double* beta64[3];  // float64 face coefficients (T = double), else nullptr
+    const double* b;       // right-hand side (mean removed on the fly, times sign)
+    double sign;
+    double* x;             // float64 solution (warm start)
+    T* r;                  // inner residual (= level-0 f of the V-cycle)
+    T* z;                  // preconditioned residual (= level-0 x)
+    T* p[2];               // search directions (double buffered)
+    T* q;                  // A p
+    T* e;                  // inner solution (correction of x)
+};
+
+template <typename T, int DIM>
+void launch_beta0(const Dims& g, const Phys& ph, const T* phi, double* const* beta,
+                  cudaStream_t s);
 template <typename T, int DIM>
 void launch_mg_setup(const Dims& g0, const Phys& ph, const T* phi, MGHier<T>& H, cudaStream_t s);
 template <typename T, int DIM>
 void launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc,
                    cudaStream_t s, Prof* pr);
 template <typename T, int DIM>
-void launch_cg_start(const Dims& g, const Phys& ph, const T* phi, const double* b, double sign,
-                     double* x, double* r, T* rT, RedBuf rb, CGScalars* sc, cudaStream_t s);
+void launch_ir_residual(const Dims& g, const Phys& ph, const SolveIO<T, DIM>& io, int first,
+                        RedBuf rb, CGScalars* sc, cudaStream_t s);
 template <typename T, int DIM>
-void launch_cg_dots(const Dims& g, const T* z, const double* r, const double* q, int first,
-                    RedBuf rb, CGScalars* sc, cudaStream_t s);
+void launch_ir_addcorr(const Dims& g, const SolveIO<T, DIM>& io, CGScalars* sc, cudaStream_t s);
 template <typename T, int DIM>
-void launch_cg_dir(const Dims& g, const Phys& ph, const T* phi, const T* z, const double* p_old,
-                   double* p_new, double* q, int first, RedBuf rb, CGScalars* sc,
-                   cudaStream_t s);
+void launch_in_dots(const Dims& g, const SolveIO<T, DIM>& io, int first, RedBuf rb,
+                    CGScalars* sc, cudaStream_t s);
 template <typename T, int DIM>
-void launch_cg_update(const Dims& g, const double* p, const double* q, double* x, double* r,
-                      T* rT, RedBuf rb, CGScalars* sc, cudaStream_t s);
+void launch_in_dir(const Dims& g, const Phys& ph, const SolveIO<T, DIM>& io, int cur, int first,
+                   RedBuf rb, CGScalars* sc, cudaStream_t s);
+template <typename T, int DIM>
+void launch_in_update(const Dims& g, const SolveIO<T, DIM>& io, int cur, int first, RedBuf rb,
+                      CGScalars* sc, cudaStream_t s);
 void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s);
 
 }  // namespace pf

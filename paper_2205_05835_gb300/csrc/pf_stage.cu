@@ -18,7 +18,7 @@ __device__ __forceinline__ T clamp01(T v) { return v < T(0) ? T(0) : (v > T(1) ?
 
 template <typename T>
 __device__ __forceinline__ T rho_of(T phi, const Phys& ph) {
-    return T(ph.rho_out) + (T(ph.rho_in) - T(ph.rho_out)) * clamp01(phi);
+    return rho_of_p(phi, ph);
 }
 
 template <typename T>
@@ -34,9 +34,8 @@ __device__ __forceinline__ double dpsi64(double p) { return p * (1.0 - p) * (1.0
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
 __global__ void k_init_phi(Dims g, Phys ph, double R, int mode, double amp, T* __restrict__ phi) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= g.ncell) return;
-    Cell c = decode(idx, g);
+    for_cells(g, [&](int ci, int cj, int ck, int idx) {
+    Cell c{ci, cj, ck};
     double cx = 0.5 * g.nx * g.h, cy = 0.5 * g.ny * g.h, cz = 0.5 * g.nz * g.h;
     double x = (c.i + 0.5) * g.h - cx, y = (c.j + 0.5) * g.h - cy;
     double z = DIM == 3 ? (c.k + 0.5) * g.h - cz : 0.0;
@@ -58,12 +57,14 @@ __global__ void k_init_phi(Dims g, Phys ph, double R, int mode, double amp, T* _
         }
     }
     phi[idx] = T(0.5 * (1.0 + tanh((Rt - r) / (2.0 * ph.eps))));
+    });
 }
 
 template <typename T, int DIM>
 void launch_init_phi(const Dims& g, const Phys& ph, double R, int mode, double amp, T* phi,
                      cudaStream_t s) {
-    k_init_phi<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(g, ph, R, mode, amp, phi);
+    k_init_phi<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(g, ph, R, mode, amp,
+                                                                            phi);
 }
 
 template <typename T>
@@ -108,16 +109,15 @@ __device__ __forceinline__ void normal_at(const T* __restrict__ phi, const Nbr<D
     mag = sqrt(s);
     T den = mag + dn;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) n[d] = gr[d] / den;
+    for (int d = 0; d < DIM; ++d) n[d] = divq(gr[d], den);
 }
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* __restrict__ n1,
             T* __restrict__ n2, T* __restrict__ mu_out, T* __restrict__ kap_out) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= g.ncell) return;
-    Cell c = decode(idx, g);
+    for_cells(g, [&](int ci, int cj, int ck, int idx) {
+    Cell c{ci, cj, ck};
     Nbr<DIM> nb(c, g);
     const T inv_h = T(1.0 / g.h), inv2h = T(0.5 / g.h), inv_h2 = T(1.0 / (g.h * g.h));
     const T dn = T(ph.delta_n);
@@ -133,9 +133,9 @@ k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* _
         for (int d = 0; d < DIM; ++d)
             lap = lap + (ldg(phi, nb.ax(d, 1)) - T(2) * pc + ldg(phi, nb.ax(d, -1))) * inv_h2;
         const double sh = 6.0 * ph.sigma;
-        // double-well term in float64 (cancellation near phi = 0, 1)
-        double mu = (sh / ph.eps) * dpsi64(double(pc)) - sh * ph.eps * double(lap);
-        mu_out[idx] = T(mu);
+        // double-well term psi'(phi) in float64 (cancellation near phi = 0, 1)
+        const T dw = T((sh / ph.eps) * dpsi64(double(pc)));
+        mu_out[idx] = dw - T(sh * ph.eps) * lap;
     }
     if (kap_out) {
         T div = T(0);
@@ -150,6 +150,7 @@ k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* _
         kap_out[idx] = -div;
     }
     (void)inv_h;
+    });
 }
 
 template <typename T, int DIM>
@@ -165,8 +166,8 @@ void launch_cell_pass(const Dims& g, const Phys& ph, const T* phi, T* nrm0, T* n
     } else {
         kap = aux;
     }
-    k_cell_pass<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(g, ph, phi, nrm0, nrm1, nrm2, mu,
-                                                                kap);
+    k_cell_pass<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(g, ph, phi, nrm0, nrm1,
+                                                                              nrm2, mu, kap);
 }
 
 // ---------------------------------------------------------------------------
@@ -176,9 +177,8 @@ void launch_cell_pass(const Dims& g, const Phys& ph, const T* phi, T* nrm0, T* n
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int write_rhs) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= g.ncell) return;
-    Cell c = decode(idx, g);
+    for_cells(g, [&](int ci, int cj, int ck, int idx) {
+    Cell c{ci, cj, ck};
     Nbr<DIM> nb(c, g);
     const T h = T(g.h), inv_h = T(1.0 / g.h), inv2h = T(0.5 / g.h), inv_h2 = T(1.0 / (g.h * g.h));
     const T eps = T(ph.eps);
@@ -225,7 +225,7 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
         T kc = ldg(kap, idx);
         T third = (ph.model == 1) ? eps * sqrt(g2) * kc : pc * (T(1) - pc) * kc;
         T dp = T(dpsi64(double(pc)));
-        kphi = kphi + gam * (eps * lap - dp / eps + third);
+        kphi = kphi + gam * (eps * lap - divq(dp, eps) + third);
     }
 
     // ---------------- momentum at the low faces ----------------
@@ -290,15 +290,15 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
                 F = T(6) * sigma * kf * pf * (T(1) - pf) * dphi;
             }
         }
-        const T beta = T(1) / (T(0.5) * (rho_of(pc, ph) + rho_of(pm, ph)));
+        const T beta = divq(T(1), T(0.5) * (rho_of(pc, ph) + rho_of(pm, ph)));
         ku[d] = -adv + beta * visc + beta * F;
     }
     (void)h;
 
     if (write_rhs) {
-        io.rhs_phi[idx] = double(kphi);
+        io.rhs_phi[idx] = kphi;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) io.rhs_u[d][idx] = double(ku[d]);
+        for (int d = 0; d < DIM; ++d) io.rhs_u[d][idx] = ku[d];
         return;
     }
     // ---------------- RK stage update ----------------
@@ -325,13 +325,14 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
         for (int d = 0; d < DIM; ++d)
             io.u_out[d][idx] = ldg(io.u_n[d], idx) + (io.acc_u[d][idx] + wdt * ku[d]);
     }
+    });
 }
 
 template <typename T, int DIM>
 void launch_stage(const Dims& g, const Phys& ph, const StageIO<T>& io, int stage, int scheme,
                   double wdt, double cdt, int write_rhs, cudaStream_t s) {
-    k_stage<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(g, ph, io, stage, scheme, T(wdt),
-                                                            T(cdt), write_rhs);
+    k_stage<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(g, ph, io, stage, scheme,
+                                                                          T(wdt), T(cdt), write_rhs);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,21 +370,23 @@ k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T
              double inv_tau, double* __restrict__ b, RedBuf rb, CGScalars* sc) {
     double s = 0.0;
     const double inv_h = 1.0 / g.h;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.ncell;
-         idx += gridDim.x * blockDim.x) {
-        Cell c = decode(idx, g);
-        int ip = c.i + 1 == g.nx ? idx - c.i : idx + 1;
-        int jp = c.j + 1 == g.ny ? idx - c.j * g.nx : idx + g.nx;
-        double dv = (double(u0[ip]) - double(u0[idx])) * inv_h;
-        dv += (double(u1[jp]) - double(u1[idx])) * inv_h;
-        if (DIM == 3) {
-            int kp = c.k + 1 == g.nz ? idx - c.k * g.nx * g.ny : idx + g.nx * g.ny;
-            dv += (double(u2[kp]) - double(u2[idx])) * inv_h;
+    for_cells(g, [&](int i, int j, int k, int idx) {
+        const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
+        double dv;
+        if (sizeof(T) == sizeof(double)) {
+            dv = (double(u0[nb.m[1]]) - double(u0[idx])) * inv_h;
+            dv += (double(u1[nb.m[3]]) - double(u1[idx])) * inv_h;
+            if (DIM == 3) dv += (double(u2[nb.m[5]]) - double(u2[idx])) * inv_h;
+        } else {
+            // float32 velocities: the differences are exact in float64 and summed there
+            dv = (double(u0[nb.m[1]]) - double(u0[idx])) + (double(u1[nb.m[3]]) - double(u1[idx]));
+            if (DIM == 3) dv += double(u2[nb.m[5]]) - double(u2[idx]);
+            dv *= inv_h;
         }
         dv *= inv_tau;
         b[idx] = dv;
         s += dv;
-    }
+    });
     double v[1] = {s}, tot[1];
     const int mode[1] = {0};
     if (grid_reduce<1>(v, mode, rb, tot) && threadIdx.x == 0) sc->mean_b = tot[0] / g.ncell;
@@ -392,7 +395,7 @@ k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T
 template <typename T, int DIM>
 void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double* b, RedBuf rb,
                        CGScalars* sc, cudaStream_t s) {
-    k_divergence<T, DIM><<<red_grid(g.ncell), kThreads, 0, s>>>(
+    k_divergence<T, DIM><<<row_grid(g, kThreads, kRedBlocks), kThreads, 0, s>>>(
         g, u[0], u[1], DIM == 3 ? u[2] : u[0], inv_tau, b, rb, sc);
 }
 
@@ -401,37 +404,45 @@ void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double*
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
-k_correct(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ s0,
+k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__ b0,
+          const double* __restrict__ b1, const double* __restrict__ b2, const T* __restrict__ s0,
           const T* __restrict__ s1, const T* __restrict__ s2, const double* __restrict__ p,
           double tau, T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= g.ncell) return;
-    Cell c = decode(idx, g);
     const double inv_h = 1.0 / g.h;
-    const T pc = ldg(phi, idx);
-    const double rc = double(rho_of(pc, ph));
-    const double pp = p[idx];
-    int im[3];
-    im[0] = c.i == 0 ? idx + g.nx - 1 : idx - 1;
-    im[1] = c.j == 0 ? idx + (g.ny - 1) * g.nx : idx - g.nx;
-    im[2] = DIM == 3 ? (c.k == 0 ? idx + (g.nz - 1) * g.nx * g.ny : idx - g.nx * g.ny) : idx;
-    const T* sv[3] = {s0, s1, s2};
-    T* ov[3] = {o0, o1, o2};
+    for_cells(g, [&](int i, int j, int k, int idx) {
+        const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
+        const double pp = p[idx];
+        const T* sv[3] = {s0, s1, s2};
+        T* ov[3] = {o0, o1, o2};
+        const double* bv[3] = {b0, b1, b2};
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        double rf = 0.5 * (rc + double(rho_of(ldg(phi, im[d]), ph)));
-        double beta = 1.0 / rf;
-        double gp = (pp - p[im[d]]) * inv_h;
-        ov[d][idx] = T(double(sv[d][idx]) - tau * beta * gp);
-    }
+        for (int d = 0; d < DIM; ++d) {
+            const int m = nb.m[2 * d];
+            if (b0 != nullptr) {
+                // float64 path: the solver's float64 face coefficients
+                const double gp = (pp - p[m]) * inv_h;
+                ov[d][idx] = T(double(sv[d][idx]) - tau * bv[d][idx] * gp);
+            } else {
+                // float32 path: same beta as the pressure operator; the pressure
+                // difference is formed in float64, the update in float32
+                const float beta = beta_face32(float(phi[idx]), float(phi[m]), ph);
+                const float gp = float((pp - p[m]) * (tau * inv_h));
+                ov[d][idx] = T(float(sv[d][idx]) - beta * gp);
+            }
+        }
+    });
 }
 
 template <typename T, int DIM>
-void launch_correct(const Dims& g, const Phys& ph, const T* phi, const T* const* ustar,
-                    const double* p, double tau, T* const* uout, cudaStream_t s) {
-    k_correct<T, DIM><<<lin_grid(g.ncell), kThreads, 0, s>>>(
-        g, ph, phi, ustar[0], ustar[1], DIM == 3 ? ustar[2] : ustar[0], p, tau, uout[0], uout[1],
-        DIM == 3 ? uout[2] : uout[0]);
+void launch_correct(const Dims& g, const Phys& ph, const T* phi, const double* const* beta64,
+                    const T* const* ustar, const double* p, double tau, T* const* uout,
+                    cudaStream_t s) {
+    const double* b0 = beta64 ? beta64[0] : nullptr;
+    const double* b1 = beta64 ? beta64[1] : nullptr;
+    const double* b2 = beta64 ? beta64[DIM == 3 ? 2 : 1] : nullptr;
+    k_correct<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
+        g, ph, phi, b0, b1, b2, ustar[0], ustar[1], DIM == 3 ? ustar[2] : ustar[0], p, tau, uout[0],
+        uout[1], DIM == 3 ? uout[2] : uout[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -445,14 +456,10 @@ k_diag(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ u0,
     double mass = 0, ke = 0, se = 0, umax = 0, pmin = 1e308, pmax = -1e308;
     double pin = 0, pout = 0, nin = 0, nout = 0, psum = 0, bad = 0;
     const double inv_h = 1.0 / g.h, sh = 6.0 * ph.sigma;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.ncell;
-         idx += gridDim.x * blockDim.x) {
-        Cell c = decode(idx, g);
+    for_cells(g, [&](int ci, int cj, int ck, int idx) {
+        const Nb6 nb = nb6<DIM>(g, ci, cj, ck, idx);
         double pc = double(phi[idx]);
-        int im[3];
-        im[0] = c.i == 0 ? idx + g.nx - 1 : idx - 1;
-        im[1] = c.j == 0 ? idx + (g.ny - 1) * g.nx : idx - g.nx;
-        im[2] = DIM == 3 ? (c.k == 0 ? idx + (g.nz - 1) * g.nx * g.ny : idx - g.nx * g.ny) : idx;
+        int im[3] = {nb.m[0], nb.m[2], nb.m[4]};
         const T* uv[3] = {u0, u1, u2};
         double rc = double(rho_of(T(pc), ph));
         double grad2 = 0.0;
@@ -476,7 +483,7 @@ k_diag(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ u0,
         if (pc >= 0.999) { pin += pp; nin += 1.0; }
         if (pc <= 0.001) { pout += pp; nout += 1.0; }
         if (!isfinite(pc) || !isfinite(pp)) bad += 1.0;
-    }
+    });
     double v[12] = {mass, ke, se, umax, -pmin, pmax, pin, pout, nin, nout, psum, bad};
     const int mode[12] = {0, 0, 0, 1, 1, 1, 0, 0, 0, 0, 0, 0};
     double tot[12];
@@ -501,7 +508,7 @@ k_diag(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ u0,
 template <typename T, int DIM>
 void launch_diagnostics(const Dims& g, const Phys& ph, const T* phi, const T* const* u,
                         const double* p, RedBuf rb, DiagOut* out, cudaStream_t s) {
-    k_diag<T, DIM><<<red_grid(g.ncell), kThreads, 0, s>>>(g, ph, phi, u[0], u[1],
+    k_diag<T, DIM><<<row_grid(g, kThreads, kRedBlocks), kThreads, 0, s>>>(g, ph, phi, u[0], u[1],
                                                            DIM == 3 ? u[2] : u[0], p, rb, out);
 }
 
@@ -519,8 +526,9 @@ void launch_diagnostics(const Dims& g, const Phys& ph, const T* phi, const T* co
                                      RedBuf, cudaStream_t);                                     \
     template void launch_divergence<T, D>(const Dims&, const T* const*, double, double*,        \
                                           RedBuf, CGScalars*, cudaStream_t);                    \
-    template void launch_correct<T, D>(const Dims&, const Phys&, const T*, const T* const*,     \
-                                       const double*, double, T* const*, cudaStream_t);         \
+    template void launch_correct<T, D>(const Dims&, const Phys&, const T*, const double* const*, \
+                                       const T* const*, const double*, double, T* const*,       \
+                                       cudaStream_t);                                           \
     template void launch_diagnostics<T, D>(const Dims&, const Phys&, const T*, const T* const*, \
                                            const double*, RedBuf, DiagOut*, cudaStream_t);
 

@@ -179,6 +179,35 @@ typedef struct {
 pf_status pf_profile_enable(pf_ctx* ctx, int enable);
 int pf_profile_read(pf_ctx* ctx, pf_profile_entry* out, int max_entries, int reset);
 
+/* Allocation-free pressure solve, for callers that cannot allocate device
+ * memory: code that runs where cudaMalloc is forbidden or unsafe (inside a
+ * region being captured into a CUDA graph by another library, under a host
+ * framework whose memory pool owns all device memory, or after start-up in a
+ * real-time loop that must not allocate). It solves the same system as
+ * pf_poisson_solve, -div(grad x / rho(phi)) = rhs with the mean of rhs
+ * removed and x returned with zero mean, without a context or workspace: all
+ * scratch lives in one fixed array inside the library of
+ * PF_STATIC_SCRATCH_BYTES (64 MiB), which every GPU that loads the library
+ * holds until the process exits. Capacity: about 100 bytes per cell in
+ * float64 (about 650k cells, e.g. 80^3 or 512^2) and about 47 bytes per cell
+ * in mixed precision (about 1.4M cells, e.g. 112^3); larger grids return
+ * PF_ERR_INVALID with the sizes in pf_last_error(NULL).
+ * prm: as for pf_init (the fields of the pressure solve are used: dim, n, L,
+ * rho_in, rho_out, precision, poisson_rtol, poisson_maxit, mg_pre, mg_post).
+ * phi, rhs: float64 device arrays of nx*ny*nz (inputs); x: float64 device
+ * array, initial guess on entry and solution on exit. stream: cudaStream_t as
+ * void*. Synchronises the stream before returning. iters, relres: optional.
+ * Returns PF_ERR_NOT_CONVERGED (x still written) when poisson_maxit is hit.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make it before any stream capture. The array keeps the
+ * last call's contents and every call clears what must start at zero; calls
+ * that overlap on the GPU (two streams or threads at once) share the array and
+ * race. The paper has no counterpart: this is a deployment variant of the
+ * projection's Poisson solve. */
+#define PF_STATIC_SCRATCH_BYTES (64u << 20)
+pf_status pf_poisson_solve_static(const pf_params* prm, const double* phi, const double* rhs,
+                                  double* x, void* stream, int* iters, double* relres);
+
 /* Wait for all work of the context and return the latched device status. */
 pf_status pf_sync(pf_ctx* ctx);
 

@@ -25,7 +25,7 @@ PF_FIELD_PHI, PF_FIELD_U, PF_FIELD_V, PF_FIELD_W, PF_FIELD_P = 0, 1, 2, 3, 4
 SYMBOLS = ["pf_workspace_size", "pf_init", "pf_step", "pf_project", "pf_diagnostics",
            "pf_get_field", "pf_set_field", "pf_state_bytes", "pf_get_state", "pf_set_state",
            "pf_eval_rhs", "pf_poisson_solve", "pf_sync", "pf_destroy", "pf_last_error",
-           "pf_profile_enable", "pf_profile_read"]
+           "pf_profile_enable", "pf_profile_read", "pf_poisson_solve_static"]
 
 
 class pf_params(ctypes.Structure):
@@ -95,6 +95,7 @@ def _load():
         "pf_last_error": (ctypes.c_char_p, [vp]),
         "pf_profile_enable": (i32, [vp, i32]),
         "pf_profile_read": (i32, [vp, P(pf_profile_entry), i32, i32]),
+        "pf_poisson_solve_static": (i32, [P(pf_params), vp, vp, vp, vp, P(i32), P(f64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -191,6 +192,17 @@ def pf_profile_read(ctx, reset: bool = True) -> dict:
     arr = (pf_profile_entry * 32)()
     n = LIB.pf_profile_read(ctx, arr, 32, 1 if reset else 0)
     return {arr[i].name.decode(): (arr[i].launches, arr[i].ms) for i in range(min(n, 32))}
+
+
+def pf_poisson_solve_static(params: pf_params, phi: int, rhs: int, x: int, stream: int | None):
+    """Allocation-free solve (device pointers); returns (status, iterations, relres)."""
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = LIB.pf_poisson_solve_static(ctypes.byref(params), phi, rhs, x, stream, ctypes.byref(it),
+                                     ctypes.byref(rel))
+    if st not in (PF_OK, PF_ERR_NOT_CONVERGED):
+        _check(st, None)
+    return st, it.value, rel.value
 
 
 def pf_last_error(ctx=None) -> str:

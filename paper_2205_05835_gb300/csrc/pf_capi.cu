@@ -225,8 +225,11 @@ struct ImplT final : Impl {
         H.coarse_sweeps = sweeps < 8 ? 8 : (sweeps > 2000 ? 2000 : sweeps);
     }
 
+    bool owns_host = false;
+
     ~ImplT() override {
         prof.destroy();
+        if (!owns_host) return;
         if (h_sc) cudaFreeHost(h_sc);
         if (h_dout) cudaFreeHost(h_dout);
         if (h_scalar) cudaFreeHost(h_scalar);
@@ -274,7 +277,78 @@ struct ImplT final : Impl {
         dsum = cv.take<double>(4);
     }
 
+    // Layout of a pressure solve alone (phi plus the solver's vectors), used by
+    // the allocation-free entry point; the stage fields stay unset.
+    void carve_solver_only(Carver& cv) {
+        const size_t n = g.ncell;
+        phiN = cv.take<T>(n);
+        p = cv.take<double>(n);
+        b = cv.take<double>(n);
+        rT = cv.take<T>(n);
+        z = cv.take<T>(n);
+        pd[0] = cv.take<T>(n);
+        pd[1] = cv.take<T>(n);
+        qT = cv.take<T>(n);
+        eT = cv.take<T>(n);
+        for (int d = 0; d < 3; ++d)
+            beta64[d] = (sizeof(T) == sizeof(double) && d < DIM) ? cv.take<double>(n) : nullptr;
+        H.lev[0].x = z;
+        H.lev[0].f = rT;
+        for (int d = 0; d < 3; ++d)
+            H.lev[0].beta[d] = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(beta64[d]) : nullptr;
+        for (int l = 1; l < H.nlev; ++l) {
+            const size_t m = H.lev[l].g.ncell;
+            H.lev[l].x = cv.take<T>(m);
+            H.lev[l].f = cv.take<T>(m);
+            for (int d = 0; d < 3; ++d) H.lev[l].beta[d] = d < DIM ? cv.take<T>(m) : nullptr;
+        }
+        rb.part = cv.take<double>(kRedBlocks * 16);
+        rb.counter = cv.take<unsigned int>(4);
+        sc = cv.take<CGScalars>(1);
+        dsum = cv.take<double>(4);
+    }
+
+    // One pressure solve on the solver-only layout without any allocation:
+    // phi, rhs and x are float64 device arrays; host mirrors are caller-provided
+    // pageable memory. Everything that must start at zero is cleared here.
+    pf_status solve_static(const double* phi_in, const double* rhs, double* x, CGScalars* hsc,
+                           int* iters, double* relres) {
+        h_sc = hsc;
+        const size_t n = g.ncell;
+        CK(cudaMemsetAsync(rb.counter, 0, 4 * sizeof(unsigned int), st));
+        CGScalars s0;
+        memset(&s0, 0, sizeof(s0));
+        s0.rtol2 = prm.poisson_rtol * prm.poisson_rtol;
+        s0.maxit = prm.poisson_maxit;
+        s0.eta2_min = sizeof(T) == sizeof(double) ? 0.0 : 1e-8;
+        CK(cudaMemcpyAsync(sc, &s0, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
+        launch_convert_in<T>(phi_in, phiN, (int)n, st);
+        CK(cudaMemcpyAsync(b, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        launch_sum((int)n, b, rb, dsum, st);
+        double sum_b = 0.0;
+        CK(cudaMemcpyAsync(&sum_b, dsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double mean_b = sum_b / (double)n;
+        CK(cudaMemcpyAsync(&sc->mean_b, &mean_b, sizeof(double), cudaMemcpyHostToDevice, st));
+        pf_status s = solve(phiN, 1.0);
+        if (iters) *iters = last_iters;
+        if (relres) *relres = last_relres;
+        if (s != PF_OK && s != PF_ERR_NOT_CONVERGED) {
+            h_sc = nullptr;
+            return s;
+        }
+        launch_sum((int)n, p, rb, dsum, st);
+        launch_convert_out<double>(p, b, (int)n, 0.0, dsum, 1.0 / (double)n, st);
+        CK(cudaMemcpyAsync(x, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        h_sc = nullptr;
+        return s;
+    }
+
     pf_status alloc_host() {
+        owns_host = true;
         CK(cudaHostAlloc((void**)&h_sc, sizeof(CGScalars), cudaHostAllocDefault));
         CK(cudaHostAlloc((void**)&h_dout, sizeof(DiagOut), cudaHostAllocDefault));
         CK(cudaHostAlloc((void**)&h_scalar, 8 * sizeof(double), cudaHostAllocDefault));
@@ -702,9 +776,74 @@ Impl* make_impl(const pf_params& p, cudaStream_t s, std::string& err) {
     return new (std::nothrow) ImplT<double, 3>(p, s, err);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free pressure solve: scratch in a fixed device array
+// ---------------------------------------------------------------------------
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_pf_static_scratch[PF_STATIC_SCRATCH_BYTES];
+
+// Device address of the array per device, looked up once per device with that
+// device current (the host-side symbol is only a stand-in for it).
+void* g_static_scratch_addr[64] = {};
+
+template <typename T, int DIM>
+pf_status run_static_solve(const pf_params& prm, cudaStream_t st, void* scratch,
+                           const double* phi, const double* rhs, double* x, int* iters,
+                           double* relres, std::string& err) {
+    ImplT<T, DIM> im(prm, st, err);
+    Carver size_cv{nullptr};
+    im.carve_solver_only(size_cv);
+    if (size_cv.off > (size_t)PF_STATIC_SCRATCH_BYTES) {
+        err = "grid too large for the static scratch of pf_poisson_solve_static (" +
+              std::to_string(size_cv.off) + " bytes needed, " +
+              std::to_string((size_t)PF_STATIC_SCRATCH_BYTES) + " available)";
+        return PF_ERR_INVALID;
+    }
+    Carver cv{static_cast<char*>(scratch)};
+    im.carve_solver_only(cv);
+    CGScalars host_sc;
+    return im.solve_static(phi, rhs, x, &host_sc, iters, relres);
+}
+
 }  // namespace
 
 extern "C" {
+
+pf_status pf_poisson_solve_static(const pf_params* prm, const double* phi, const double* rhs,
+                                  double* x, void* stream, int* iters, double* relres) {
+    std::string why;
+    pf_status s = validate(prm, why);
+    if (s != PF_OK) { g_init_error = why; return s; }
+    if (!phi || !rhs || !x) { g_init_error = "phi, rhs and x must be device pointers"; return PF_ERR_INVALID; }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        g_init_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return PF_ERR_CUDA;
+    }
+    if (!g_static_scratch_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_pf_static_scratch);
+        if (e != cudaSuccess || !ptr) {
+            g_init_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return PF_ERR_CUDA;
+        }
+        g_static_scratch_addr[dev] = ptr;
+    }
+    void* scratch = g_static_scratch_addr[dev];
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::string err;
+    const bool mixed = prm->precision == PF_MIXED;
+    if (prm->dim == 2)
+        s = mixed ? run_static_solve<float, 2>(*prm, st, scratch, phi, rhs, x, iters, relres, err)
+                  : run_static_solve<double, 2>(*prm, st, scratch, phi, rhs, x, iters, relres, err);
+    else
+        s = mixed ? run_static_solve<float, 3>(*prm, st, scratch, phi, rhs, x, iters, relres, err)
+                  : run_static_solve<double, 3>(*prm, st, scratch, phi, rhs, x, iters, relres, err);
+    if (s != PF_OK) g_init_error = err;
+    return s;
+}
+
 
 pf_status pf_workspace_size(const pf_params* prm, size_t* bytes) {
     std::string why;

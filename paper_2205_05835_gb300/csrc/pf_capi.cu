@@ -161,6 +161,7 @@ struct ImplT final : Impl {
     T *nrm[3], *aux;
     double *p, *b;
     double* beta64[3];   // float64 face coefficients (float64 path only)
+    float* beta32[3] = {nullptr, nullptr, nullptr};  // float32 face coefficients (mixed path)
     T *rT, *z, *pd[2], *qT, *eT;
     MGHier<T> H;
     RedBuf rb;
@@ -180,11 +181,7 @@ struct ImplT final : Impl {
 
     ImplT(const pf_params& p_, cudaStream_t s_, std::string& e_) : prm(p_), st(s_), err(e_) {
         prof.st = s_;
-        g.nx = prm.n[0];
-        g.ny = prm.n[1];
-        g.nz = DIM == 3 ? prm.n[2] : 1;
-        g.ncell = g.nx * g.ny * g.nz;
-        g.h = prm.L / prm.n[0];
+        g = make_dims(prm.n[0], prm.n[1], DIM == 3 ? prm.n[2] : 1, prm.L / prm.n[0]);
         ph.dim = DIM;
         ph.model = prm.model;
         ph.force = prm.force;
@@ -195,6 +192,15 @@ struct ImplT final : Impl {
         ph.mu_in = prm.mu_in;
         ph.mu_out = prm.mu_out;
         ph.delta_n = prm.delta_n;
+        ph.drho = prm.rho_in - prm.rho_out;
+        ph.dmu = prm.mu_in - prm.mu_out;
+        ph.sigma_f = float(prm.sigma);
+        ph.eps_f = float(prm.eps);
+        ph.rho_out_f = float(prm.rho_out);
+        ph.drho_f = float(prm.rho_in) - float(prm.rho_out);
+        ph.mu_out_f = float(prm.mu_out);
+        ph.dmu_f = float(prm.mu_in) - float(prm.mu_out);
+        ph.delta_n_f = float(prm.delta_n);
         for (int d = 0; d < 3; ++d) uN[d] = uS[d] = uStar[d] = accu[d] = nrm[d] = nullptr;
         // multigrid hierarchy geometry
         H.nlev = 1;
@@ -204,15 +210,10 @@ struct ImplT final : Impl {
             bool ok = (f.nx % 2 == 0) && (f.ny % 2 == 0) && (DIM == 2 || f.nz % 2 == 0) &&
                       f.nx >= 4 && f.ny >= 4 && (DIM == 2 || f.nz >= 4);
             if (!ok) break;
-            Dims c;
-            c.nx = f.nx / 2;
-            c.ny = f.ny / 2;
-            c.nz = DIM == 3 ? f.nz / 2 : 1;
-            c.ncell = c.nx * c.ny * c.nz;
-            c.h = f.h * 2.0;
-            H.lev[H.nlev].g = c;
+            H.lev[H.nlev].g = make_dims(f.nx / 2, f.ny / 2, DIM == 3 ? f.nz / 2 : 1, f.h * 2.0);
             ++H.nlev;
         }
+        for (int l = 0; l < kMaxLevels; ++l) H.lev[l].x2 = nullptr;
         H.first_coarse = H.nlev - 1;
         for (int l = 0; l < H.nlev; ++l)
             if (H.lev[l].g.ncell <= 4096) { H.first_coarse = l; break; }
@@ -259,16 +260,24 @@ struct ImplT final : Impl {
         eT = cv.take<T>(n);
         for (int d = 0; d < 3; ++d)
             beta64[d] = (sizeof(T) == sizeof(double) && d < DIM) ? cv.take<double>(n) : nullptr;
+        for (int d = 0; d < 3; ++d)
+            beta32[d] = (sizeof(T) == sizeof(float) && d < DIM) ? cv.take<float>(n) : nullptr;
         H.lev[0].x = z;
         H.lev[0].f = rT;
         for (int d = 0; d < 3; ++d)
-            H.lev[0].beta[d] = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(beta64[d]) : nullptr;
+            H.lev[0].beta[d] = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(beta64[d])
+                                                           : reinterpret_cast<T*>(beta32[d]);
         for (int l = 1; l < H.nlev; ++l) {
             const size_t m = H.lev[l].g.ncell;
             H.lev[l].x = cv.take<T>(m);
             H.lev[l].f = cv.take<T>(m);
             for (int d = 0; d < 3; ++d) H.lev[l].beta[d] = d < DIM ? cv.take<T>(m) : nullptr;
         }
+        // second buffers for the one-pass out-of-place sweeps (3D float32 levels
+        // below the single-CTA levels)
+        if (DIM == 3 && sizeof(T) == sizeof(float))
+            for (int l = 0; l < H.first_coarse; ++l)
+                H.lev[l].x2 = sweep3d_ok(H.lev[l].g) ? cv.take<T>(H.lev[l].g.ncell) : nullptr;
         rb.part = cv.take<double>(kRedBlocks * 16);
         rb.counter = cv.take<unsigned int>(4);
         sc = cv.take<CGScalars>(1);
@@ -407,8 +416,8 @@ struct ImplT final : Impl {
         pf_status s = solve(phi, -1.0);
         if (s != PF_OK) return s;
         prof.begin(KC_CORRECT);
-        launch_correct<T, DIM>(g, ph, phi, sizeof(T) == sizeof(double) ? beta64 : nullptr, uin_c,
-                               p, tau, uout, st);
+        launch_correct<T, DIM>(g, ph, phi, sizeof(T) == sizeof(double) ? beta64 : nullptr,
+                               beta32[0] ? beta32 : nullptr, uin_c, p, tau, uout, st);
         prof.end();
         return PF_OK;
     }
@@ -417,6 +426,7 @@ struct ImplT final : Impl {
         SolveIO<T, DIM> io;
         io.phi = phi;
         for (int d = 0; d < 3; ++d) io.beta64[d] = sizeof(T) == sizeof(double) ? beta64[d] : nullptr;
+        for (int d = 0; d < 3; ++d) io.beta32[d] = sizeof(T) == sizeof(float) ? beta32[d] : nullptr;
         io.b = b;
         io.sign = sign;
         io.x = p;
@@ -439,10 +449,14 @@ struct ImplT final : Impl {
     // A x = sign (b - mean b): float64 iterative refinement around inner
     // MG-preconditioned CG in T, warm start from x = p
     pf_status solve(const T* phi, double sign) {
-        const SolveIO<T, DIM> io = solve_io(phi, sign);
+        SolveIO<T, DIM> io = solve_io(phi, sign);
         if (sizeof(T) == sizeof(double)) {
             prof.begin(KC_BETA0);
             launch_beta0<T, DIM>(g, ph, phi, beta64, st);
+            prof.end();
+        } else if (beta32[0] != nullptr) {
+            prof.begin(KC_BETA0);
+            launch_beta0_32<DIM>(g, ph, reinterpret_cast<const float*>(phi), beta32, st);
             prof.end();
         }
         prof.begin(KC_COARSEN);
@@ -459,7 +473,7 @@ struct ImplT final : Impl {
             int cur = 0;
             for (int it = 0; it <= prm.poisson_maxit + poll_every; ++it) {
                 const int first = (it == 0);
-                launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof);
+                io.z = launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof);
                 prof.begin(KC_CG_DOTS);
                 launch_in_dots<T, DIM>(g, io, first, rb, sc, st);
                 prof.end();

@@ -56,9 +56,9 @@ __device__ __forceinline__ T ldg(const T* p, int i) { return __ldg(p + i); }
 
 // Density (linear in clip(phi, 0, 1), phi = 1 the drop).
 template <typename T>
-__device__ __forceinline__ T rho_of_p(T phi, const Phys& ph) {
-    T c = phi < T(0) ? T(0) : (phi > T(1) ? T(1) : phi);
-    return T(ph.rho_out) + (T(ph.rho_in) - T(ph.rho_out)) * c;
+__device__ __forceinline__ T rho_of_p(T phi, const PC<T>& c) {
+    const T s = phi < T(0) ? T(0) : (phi > T(1) ? T(1) : phi);
+    return c.rho_out + c.drho * s;
 }
 
 // 1 / rho_f of the face between two cells in float32: a correctly rounded
@@ -68,8 +68,7 @@ __device__ __forceinline__ T rho_of_p(T phi, const Phys& ph) {
 // operator is reproducible bit for bit by any IEEE float32 evaluation.
 __device__ __forceinline__ float rho32(float phi, const Phys& ph) {
     const float c = phi < 0.f ? 0.f : (phi > 1.f ? 1.f : phi);
-    const float ro = float(ph.rho_out), dr = __fsub_rn(float(ph.rho_in), float(ph.rho_out));
-    return __fadd_rn(ro, __fmul_rn(dr, c));
+    return __fadd_rn(ph.rho_out_f, __fmul_rn(ph.drho_f, c));
 }
 __device__ __forceinline__ float beta_face32(float pa, float pb, const Phys& ph) {
     return __frcp_rn(__fmul_rn(0.5f, __fadd_rn(rho32(pa, ph), rho32(pb, ph))));

@@ -12,18 +12,60 @@ constexpr int kMaxLevels = 16;
 constexpr int kRedBlocks = 152 * 8;   // fixed grid of every reduction kernel (deterministic sums)
 constexpr int kThreads = 256;
 
-// Geometry of one grid level (periodic, uniform spacing h).
+// Geometry of one grid level (periodic, uniform spacing h). The inverse
+// spacings are formed once on the host (a float64 division per cell would run
+// on GB300's narrow float64 pipe).
 struct Dims {
     int nx, ny, nz;
     int ncell;
     double h;
+    double ih, i2h, ih2;      // 1/h, 1/(2h), 1/h^2
+    float ihf, i2hf, ih2f;
 };
+inline Dims make_dims(int nx, int ny, int nz, double h) {
+    Dims g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.ncell = nx * ny * nz;
+    g.h = h;
+    g.ih = 1.0 / h;
+    g.i2h = 0.5 / h;
+    g.ih2 = 1.0 / (h * h);
+    g.ihf = float(g.ih);
+    g.i2hf = float(g.i2h);
+    g.ih2f = float(g.ih2);
+    return g;
+}
+// the inverse spacings in the arithmetic type of a kernel
+__host__ __device__ inline float ih_of(const Dims& g, float) { return g.ihf; }
+__host__ __device__ inline double ih_of(const Dims& g, double) { return g.ih; }
+__host__ __device__ inline float i2h_of(const Dims& g, float) { return g.i2hf; }
+__host__ __device__ inline double i2h_of(const Dims& g, double) { return g.i2h; }
+__host__ __device__ inline float ih2_of(const Dims& g, float) { return g.ih2f; }
+__host__ __device__ inline double ih2_of(const Dims& g, double) { return g.ih2; }
 
-// Physical and model constants of a context, passed by value to kernels.
+// Physical and model constants of a context, passed by value to kernels. The
+// float copies and differences are formed once on the host so that no kernel
+// converts a double per cell (conversions run on GB300's narrow float64 pipe).
 struct Phys {
     int dim, model, force;
     double sigma, eps, rho_in, rho_out, mu_in, mu_out, delta_n;
+    double drho, dmu;                     // rho_in - rho_out, mu_in - mu_out
+    float sigma_f, eps_f, rho_out_f, drho_f, mu_out_f, dmu_f, delta_n_f;
 };
+
+// The constants in the arithmetic type T of a kernel.
+template <typename T>
+struct PC {
+    T sigma, eps, rho_out, drho, mu_out, dmu, delta_n;
+};
+__host__ __device__ inline PC<float> pc_of(const Phys& p, float) {
+    return PC<float>{p.sigma_f, p.eps_f, p.rho_out_f, p.drho_f, p.mu_out_f, p.dmu_f, p.delta_n_f};
+}
+__host__ __device__ inline PC<double> pc_of(const Phys& p, double) {
+    return PC<double>{p.sigma, p.eps, p.rho_out, p.drho, p.mu_out, p.dmu, p.delta_n};
+}
 
 // Pointers of the state a stage kernel reads and writes. T is the storage type.
 template <typename T>
@@ -75,7 +117,14 @@ struct MGLevel {
     T* x;          // correction
     T* f;          // right-hand side
     T* beta[3];    // face coefficients 1/rho_f (nullptr on level 0: computed from phi)
+    T* x2;         // second correction buffer for out-of-place sweeps (nullptr: in place)
 };
+
+// One-pass red-black Gauss-Seidel sweep of a 3D float32 level (pf_mg3d.cu).
+bool sweep3d_ok(const Dims& g);
+void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
+                    float* xout, const MGLevel<float>* C, int first_color, const CGScalars* sc,
+                    cudaStream_t s);
 
 template <typename T>
 struct MGHier {
@@ -144,8 +193,8 @@ void launch_gamma(const Dims& g, const T* const* u, double gamma_fixed, double g
                   double* gamma, RedBuf rb, cudaStream_t s);
 template <typename T, int DIM>
 void launch_correct(const Dims& g, const Phys& ph, const T* phi, const double* const* beta64,
-                    const T* const* ustar, const double* p, double tau, T* const* uout,
-                    cudaStream_t s);
+                    const float* const* beta32, const T* const* ustar, const double* p,
+                    double tau, T* const* uout, cudaStream_t s);
 template <typename T, int DIM>
 void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double* b, RedBuf rb,
                        CGScalars* sc, cudaStream_t s);
@@ -159,6 +208,7 @@ template <typename T, int DIM>
 struct SolveIO {
     const T* phi;          // phase field defining rho
     const double* beta64[3];  // float64 face coefficients (T = double), else nullptr
+    const float* beta32[3];   // float32 face coefficients (T = float), else nullptr
     const double* b;       // right-hand side (mean removed on the fly, times sign)
     double sign;
     double* x;             // float64 solution (warm start)
@@ -172,11 +222,15 @@ struct SolveIO {
 template <typename T, int DIM>
 void launch_beta0(const Dims& g, const Phys& ph, const T* phi, double* const* beta,
                   cudaStream_t s);
+template <int DIM>
+void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
+                     cudaStream_t s);
 template <typename T, int DIM>
 void launch_mg_setup(const Dims& g0, const Phys& ph, const T* phi, MGHier<T>& H, cudaStream_t s);
+// Runs one V-cycle; returns the level-0 buffer that holds the result.
 template <typename T, int DIM>
-void launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc,
-                   cudaStream_t s, Prof* pr);
+T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc,
+                 cudaStream_t s, Prof* pr);
 template <typename T, int DIM>
 void launch_ir_residual(const Dims& g, const Phys& ph, const SolveIO<T, DIM>& io, int first,
                         RedBuf rb, CGScalars* sc, cudaStream_t s);

@@ -25,7 +25,7 @@ namespace pf {
 template <typename T, int DIM>
 __device__ __forceinline__ void face_w(const MGLevel<T>& L, const T* __restrict__ phi,
                                        const Phys& ph, int idx, const Nb6& nb, T (&w)[6]) {
-    const T ih2 = T(1.0 / (L.g.h * L.g.h));
+    const T ih2 = ih2_of(L.g, T());
     if (L.beta[0] == nullptr) {
         // level 0, float path: from phi
         const float pc = float(__ldg(phi + idx));
@@ -188,15 +188,42 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_beta0(Dims g, Phys ph, const T* __restrict__ phi, double* __restrict__ b0,
         double* __restrict__ b1, double* __restrict__ b2) {
+    const PC<double> pc = pc_of(ph, double());
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
-        const double rc = rho_of_p(double(__ldg(phi + idx)), ph);
+        const double rc = rho_of_p(double(__ldg(phi + idx)), pc);
         double* bb[3] = {b0, b1, b2};
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-            bb[d][idx] = 1.0 / (0.5 * (rc + rho_of_p(double(__ldg(phi + nb.m[2 * d])), ph)));
+            bb[d][idx] = 1.0 / (0.5 * (rc + rho_of_p(double(__ldg(phi + nb.m[2 * d])), pc)));
     });
 }
+
+// float32 face coefficients of the mixed path (the same beta_face32 as every
+// kernel that evaluates them from phi)
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_beta0_32(Dims g, Phys ph, const float* __restrict__ phi, float* __restrict__ b0,
+           float* __restrict__ b1, float* __restrict__ b2) {
+    for_cells(g, [&](int i, int j, int k, int idx) {
+        const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
+        const float pc = __ldg(phi + idx);
+        b0[idx] = beta_face32(pc, __ldg(phi + nb.m[0]), ph);
+        b1[idx] = beta_face32(pc, __ldg(phi + nb.m[2]), ph);
+        if (DIM == 3) b2[idx] = beta_face32(pc, __ldg(phi + nb.m[4]), ph);
+    });
+}
+
+template <int DIM>
+void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
+                     cudaStream_t s) {
+    k_beta0_32<DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
+        g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1]);
+}
+template void launch_beta0_32<2>(const Dims&, const Phys&, const float*, float* const*,
+                                 cudaStream_t);
+template void launch_beta0_32<3>(const Dims&, const Phys&, const float*, float* const*,
+                                 cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // single-CTA kernel for all levels >= first_coarse
@@ -292,40 +319,101 @@ void launch_beta0(const Dims& g, const Phys& ph, const T* phi, double* const* be
         g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1]);
 }
 
+// Tiled one-pass sweeps apply to 3D float32 levels with even sizes and an
+// out-of-place buffer; every other level uses the half-sweep kernels.
 template <typename T, int DIM>
-void launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc,
-                   cudaStream_t s, Prof* pr) {
+static bool tiled_level(const MGLevel<T>& L) {
+    if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        return L.x2 != nullptr && sweep3d_ok(L.g);
+    } else {
+        return false;
+    }
+}
+
+template <typename T, int DIM>
+T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc,
+                 cudaStream_t s, Prof* pr) {
     const int l0 = H.first_coarse;
-    auto gs = [&](int l, int color, int zero) {
-        const MGLevel<T>& L = H.lev[l];
-        pr->begin(l == 0 ? KC_GS0 : KC_GS);
+    T* fin[kMaxLevels];   // buffer holding each level's result
+    for (int l = l0; l < H.nlev; ++l) fin[l] = H.lev[l].x;
+    auto gs = [&](const MGLevel<T>& L, int lvl, int color, int zero) {
+        pr->begin(lvl == 0 ? KC_GS0 : KC_GS);
         k_gs<T, DIM><<<row_grid(L.g, kThreads, 1 << 30), kThreads, 0, s>>>(L, phi, ph, color,
                                                                           zero, sc);
         pr->end();
     };
+    T* pre_buf[kMaxLevels];
     for (int l = 0; l < l0; ++l) {
-        for (int p = 0; p < H.pre; ++p) {
-            gs(l, 0, p == 0);
-            gs(l, 1, 0);
+        MGLevel<T> L = H.lev[l];
+        if (tiled_level<T, DIM>(L)) {
+            if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+                T* a = L.x;
+                T* b = L.x2;
+                for (int p = 0; p < H.pre; ++p) {
+                    pr->begin(l == 0 ? KC_GS0 : KC_GS);
+                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
+                                   reinterpret_cast<const float*>(phi), ph,
+                                   p == 0 ? nullptr : reinterpret_cast<const float*>(b),
+                                   reinterpret_cast<float*>(p == 0 ? a : (p % 2 ? b : a)), nullptr,
+                                   0, sc, s);
+                    pr->end();
+                    if (p > 0) { T* t = a; a = b; b = t; }
+                }
+                pre_buf[l] = a;
+            }
+        } else {
+            for (int p = 0; p < H.pre; ++p) {
+                gs(L, l, 0, p == 0);
+                gs(L, l, 1, 0);
+            }
+            pre_buf[l] = L.x;
         }
+        L.x = pre_buf[l];
         pr->begin(KC_RESTRICT);
         k_restrict<T, DIM><<<row_grid(H.lev[l + 1].g, kThreads, 1 << 30), kThreads, 0, s>>>(
-            H.lev[l], H.lev[l + 1], phi, ph, sc);
+            L, H.lev[l + 1], phi, ph, sc);
         pr->end();
     }
     pr->begin(KC_COARSE);
     k_coarse_vcycle<T, DIM><<<1, kCoarseThreads, 0, s>>>(H, phi, ph, sc);
     pr->end();
     for (int l = l0 - 1; l >= 0; --l) {
-        pr->begin(KC_PROLONG);
-        k_prolong<T, DIM><<<row_grid(H.lev[l].g, kThreads, 1 << 30), kThreads, 0, s>>>(
-            H.lev[l], H.lev[l + 1], sc);
-        pr->end();
-        for (int p = 0; p < H.post; ++p) {
-            gs(l, 1, 0);
-            gs(l, 0, 0);
+        MGLevel<T> L = H.lev[l];
+        MGLevel<T> C = H.lev[l + 1];
+        C.x = fin[l + 1];
+        if (tiled_level<T, DIM>(L)) {
+            if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+                T* cur = pre_buf[l];
+                T* oth = cur == L.x ? L.x2 : L.x;
+                MGLevel<T> Lp = L;
+                Lp.x = cur;
+                pr->begin(KC_PROLONG);
+                k_prolong<T, DIM><<<row_grid(L.g, kThreads, 1 << 30), kThreads, 0, s>>>(Lp, C, sc);
+                pr->end();
+                for (int p = 0; p < H.post; ++p) {
+                    pr->begin(l == 0 ? KC_GS0 : KC_GS);
+                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
+                                   reinterpret_cast<const float*>(phi), ph,
+                                   reinterpret_cast<const float*>(cur), reinterpret_cast<float*>(oth),
+                                   nullptr, 1, sc, s);
+                    pr->end();
+                    T* t = cur; cur = oth; oth = t;
+                }
+                fin[l] = cur;
+            }
+        } else {
+            L.x = pre_buf[l];
+            pr->begin(KC_PROLONG);
+            k_prolong<T, DIM><<<row_grid(L.g, kThreads, 1 << 30), kThreads, 0, s>>>(L, C, sc);
+            pr->end();
+            for (int p = 0; p < H.post; ++p) {
+                gs(L, l, 1, 0);
+                gs(L, l, 0, 0);
+            }
+            fin[l] = L.x;
         }
     }
+    return fin[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -337,7 +425,7 @@ __device__ __forceinline__ double apply_A64(const Dims& g, const Phys& ph,
                                             const SolveIO<T, DIM>& io, const double* __restrict__ x,
                                             int i, int j, int k, int idx) {
     const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
-    const double ih2 = 1.0 / (g.h * g.h);
+    const double ih2 = g.ih2;
     const double xc = x[idx];
     double ax = 0.0;
     if (io.beta64[0] != nullptr) {
@@ -345,6 +433,12 @@ __device__ __forceinline__ double apply_A64(const Dims& g, const Phys& ph,
         for (int d = 0; d < DIM; ++d) {
             ax += io.beta64[d][idx] * (xc - x[nb.m[2 * d]]);
             ax += io.beta64[d][nb.m[2 * d + 1]] * (xc - x[nb.m[2 * d + 1]]);
+        }
+    } else if (io.beta32[0] != nullptr) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            ax += double(__ldg(io.beta32[d] + idx)) * (xc - x[nb.m[2 * d]]);
+            ax += double(__ldg(io.beta32[d] + nb.m[2 * d + 1])) * (xc - x[nb.m[2 * d + 1]]);
         }
     } else {
         const float pc = float(__ldg(io.phi + idx));
@@ -440,7 +534,7 @@ k_in_dir(Dims g, Phys ph, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGS
     const T beta = first ? T(0) : T(sc->beta);
     const T* __restrict__ po = cur ? io.p[1] : io.p[0];
     T* __restrict__ pn = cur ? io.p[0] : io.p[1];
-    const T ih2 = T(1.0 / (g.h * g.h));
+    const T ih2 = ih2_of(g, T());
     double pq = 0.0;
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
@@ -453,6 +547,15 @@ k_in_dir(Dims g, Phys ph, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGS
                 const T pm = first ? io.z[m] : io.z[m] + beta * po[m];
                 const int d = q >> 1;
                 const T bf = T((q & 1) ? io.beta64[d][m] : io.beta64[d][idx]);
+                ax += bf * (pc - pm);
+            }
+        } else if (io.beta32[0] != nullptr) {
+#pragma unroll
+            for (int q = 0; q < 2 * DIM; ++q) {
+                const int m = nb.m[q];
+                const T pm = first ? io.z[m] : io.z[m] + beta * po[m];
+                const int d = q >> 1;
+                const T bf = T(__ldg(io.beta32[d] + ((q & 1) ? m : idx)));
                 ax += bf * (pc - pm);
             }
         } else {
@@ -554,8 +657,8 @@ void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s) 
                                         cudaStream_t);                                           \
     template void launch_beta0<T, D>(const Dims&, const Phys&, const T*, double* const*,         \
                                      cudaStream_t);                                              \
-    template void launch_vcycle<T, D>(const Phys&, const T*, MGHier<T>&, const CGScalars*,       \
-                                      cudaStream_t, Prof*);                                      \
+    template T* launch_vcycle<T, D>(const Phys&, const T*, MGHier<T>&, const CGScalars*,         \
+                                    cudaStream_t, Prof*);                                        \
     template void launch_ir_residual<T, D>(const Dims&, const Phys&, const SolveIO<T, D>&, int,  \
                                            RedBuf, CGScalars*, cudaStream_t);                    \
     template void launch_ir_addcorr<T, D>(const Dims&, const SolveIO<T, D>&, CGScalars*,         \

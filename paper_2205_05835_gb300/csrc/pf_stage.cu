@@ -17,13 +17,13 @@ template <typename T>
 __device__ __forceinline__ T clamp01(T v) { return v < T(0) ? T(0) : (v > T(1) ? T(1) : v); }
 
 template <typename T>
-__device__ __forceinline__ T rho_of(T phi, const Phys& ph) {
-    return rho_of_p(phi, ph);
+__device__ __forceinline__ T rho_of(T phi, const PC<T>& c) {
+    return rho_of_p(phi, c);
 }
 
 template <typename T>
-__device__ __forceinline__ T eta_of(T phi, const Phys& ph) {
-    return T(ph.mu_out) + (T(ph.mu_in) - T(ph.mu_out)) * clamp01(phi);
+__device__ __forceinline__ T eta_of(T phi, const PC<T>& c) {
+    return c.mu_out + c.dmu * clamp01(phi);
 }
 
 // psi'(phi) = phi (1 - phi) (1 - 2 phi), always evaluated in float64.
@@ -116,11 +116,15 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* __restrict__ n1,
             T* __restrict__ n2, T* __restrict__ mu_out, T* __restrict__ kap_out) {
+    const PC<T> pcn = pc_of(ph, T());
+    const double sh = 6.0 * ph.sigma;
+    const double c_dw = sh / ph.eps;         // (6 sigma / eps), float64 double-well factor
+    const T c_lap = T(sh * ph.eps);          // 6 sigma eps
     for_cells(g, [&](int ci, int cj, int ck, int idx) {
     Cell c{ci, cj, ck};
     Nbr<DIM> nb(c, g);
-    const T inv_h = T(1.0 / g.h), inv2h = T(0.5 / g.h), inv_h2 = T(1.0 / (g.h * g.h));
-    const T dn = T(ph.delta_n);
+    const T inv_h = ih_of(g, T()), inv2h = i2h_of(g, T()), inv_h2 = ih2_of(g, T());
+    const T dn = pcn.delta_n;
     T n[3], mag;
     normal_at<T, DIM>(phi, nb, 0, 0, 0, inv2h, dn, n, mag);
     n0[idx] = n[0];
@@ -132,10 +136,9 @@ k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* _
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
             lap = lap + (ldg(phi, nb.ax(d, 1)) - T(2) * pc + ldg(phi, nb.ax(d, -1))) * inv_h2;
-        const double sh = 6.0 * ph.sigma;
         // double-well term psi'(phi) in float64 (cancellation near phi = 0, 1)
-        const T dw = T((sh / ph.eps) * dpsi64(double(pc)));
-        mu_out[idx] = dw - T(sh * ph.eps) * lap;
+        const T dw = T(c_dw * dpsi64(double(pc)));
+        mu_out[idx] = dw - c_lap * lap;
     }
     if (kap_out) {
         T div = T(0);
@@ -177,12 +180,14 @@ void launch_cell_pass(const Dims& g, const Phys& ph, const T* phi, T* nrm0, T* n
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int write_rhs) {
+    const PC<T> pcs = pc_of(ph, T());
+    const T gam_k = T(*io.gamma);
     for_cells(g, [&](int ci, int cj, int ck, int idx) {
     Cell c{ci, cj, ck};
     Nbr<DIM> nb(c, g);
-    const T h = T(g.h), inv_h = T(1.0 / g.h), inv2h = T(0.5 / g.h), inv_h2 = T(1.0 / (g.h * g.h));
-    const T eps = T(ph.eps);
-    const T gam = T(*io.gamma);
+    const T h = T(0), inv_h = ih_of(g, T()), inv2h = i2h_of(g, T()), inv_h2 = ih2_of(g, T());
+    const T eps = pcs.eps;
+    const T gam = gam_k;
     const T* __restrict__ phi = io.phi_s;
     const T pc = ldg(phi, idx);
 
@@ -230,7 +235,7 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
 
     // ---------------- momentum at the low faces ----------------
     T ku[3];
-    const T sigma = T(ph.sigma);
+    const T sigma = pcs.sigma;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const T* __restrict__ ud = io.u_s[d];
@@ -253,7 +258,7 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
         }
         // viscous stress divergence
         T visc = T(0);
-        const T etac = eta_of(pc, ph), etam = eta_of(pm, ph);
+        const T etac = eta_of(pc, pcs), etam = eta_of(pm, pcs);
 #pragma unroll
         for (int e = 0; e < DIM; ++e) {
             if (e == d) {
@@ -263,13 +268,13 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
             } else {
                 const T* __restrict__ ue = io.u_s[e];
                 // edge at (c - e_d/2 - e_e/2): cells c, c-e_d, c-e_e, c-e_d-e_e
-                T eta_lo = T(0.25) * (etac + etam + eta_of(ldg(phi, nb.ax(e, -1)), ph) +
-                                      eta_of(ldg(phi, nb.ax2(d, -1, e, -1)), ph));
+                T eta_lo = T(0.25) * (etac + etam + eta_of(ldg(phi, nb.ax(e, -1)), pcs) +
+                                      eta_of(ldg(phi, nb.ax2(d, -1, e, -1)), pcs));
                 T tlo = eta_lo * ((udc - ldg(ud, nb.ax(e, -1))) * inv_h +
                                   (ldg(ue, idx) - ldg(ue, im)) * inv_h);
                 // edge at (c - e_d/2 + e_e/2): cells c+e_e, c+e_e-e_d, c, c-e_d
                 const int iep = nb.ax(e, 1), iepm = nb.ax2(d, -1, e, 1);
-                T eta_hi = T(0.25) * (eta_of(ldg(phi, iep), ph) + eta_of(ldg(phi, iepm), ph) +
+                T eta_hi = T(0.25) * (eta_of(ldg(phi, iep), pcs) + eta_of(ldg(phi, iepm), pcs) +
                                       etac + etam);
                 T thi = eta_hi * ((ldg(ud, iep) - udc) * inv_h +
                                   (ldg(ue, iep) - ldg(ue, iepm)) * inv_h);
@@ -290,7 +295,7 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
                 F = T(6) * sigma * kf * pf * (T(1) - pf) * dphi;
             }
         }
-        const T beta = divq(T(1), T(0.5) * (rho_of(pc, ph) + rho_of(pm, ph)));
+        const T beta = divq(T(1), T(0.5) * (rho_of(pc, pcs) + rho_of(pm, pcs)));
         ku[d] = -adv + beta * visc + beta * F;
     }
     (void)h;
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(kThreads)
 k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
              double inv_tau, double* __restrict__ b, RedBuf rb, CGScalars* sc) {
     double s = 0.0;
-    const double inv_h = 1.0 / g.h;
+    const double inv_h = g.ih;
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
         double dv;
@@ -405,16 +410,19 @@ void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double*
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__ b0,
-          const double* __restrict__ b1, const double* __restrict__ b2, const T* __restrict__ s0,
+          const double* __restrict__ b1, const double* __restrict__ b2,
+          const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ f2,
+          const T* __restrict__ s0,
           const T* __restrict__ s1, const T* __restrict__ s2, const double* __restrict__ p,
           double tau, T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2) {
-    const double inv_h = 1.0 / g.h;
+    const double inv_h = g.ih;
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
         const double pp = p[idx];
         const T* sv[3] = {s0, s1, s2};
         T* ov[3] = {o0, o1, o2};
         const double* bv[3] = {b0, b1, b2};
+        const float* fv[3] = {f0, f1, f2};
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const int m = nb.m[2 * d];
@@ -425,7 +433,8 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
             } else {
                 // float32 path: same beta as the pressure operator; the pressure
                 // difference is formed in float64, the update in float32
-                const float beta = beta_face32(float(phi[idx]), float(phi[m]), ph);
+                const float beta = f0 != nullptr ? __ldg(fv[d] + idx)
+                                                 : beta_face32(float(phi[idx]), float(phi[m]), ph);
                 const float gp = float((pp - p[m]) * (tau * inv_h));
                 ov[d][idx] = T(float(sv[d][idx]) - beta * gp);
             }
@@ -435,14 +444,17 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
 
 template <typename T, int DIM>
 void launch_correct(const Dims& g, const Phys& ph, const T* phi, const double* const* beta64,
-                    const T* const* ustar, const double* p, double tau, T* const* uout,
-                    cudaStream_t s) {
+                    const float* const* beta32, const T* const* ustar, const double* p,
+                    double tau, T* const* uout, cudaStream_t s) {
     const double* b0 = beta64 ? beta64[0] : nullptr;
     const double* b1 = beta64 ? beta64[1] : nullptr;
     const double* b2 = beta64 ? beta64[DIM == 3 ? 2 : 1] : nullptr;
+    const float* f0 = beta32 ? beta32[0] : nullptr;
+    const float* f1 = beta32 ? beta32[1] : nullptr;
+    const float* f2 = beta32 ? beta32[DIM == 3 ? 2 : 1] : nullptr;
     k_correct<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
-        g, ph, phi, b0, b1, b2, ustar[0], ustar[1], DIM == 3 ? ustar[2] : ustar[0], p, tau, uout[0],
-        uout[1], DIM == 3 ? uout[2] : uout[0]);
+        g, ph, phi, b0, b1, b2, f0, f1, f2, ustar[0], ustar[1], DIM == 3 ? ustar[2] : ustar[0], p,
+        tau, uout[0], uout[1], DIM == 3 ? uout[2] : uout[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,19 +465,20 @@ __global__ void __launch_bounds__(kThreads)
 k_diag(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ u0,
        const T* __restrict__ u1, const T* __restrict__ u2, const double* __restrict__ p, RedBuf rb,
        DiagOut* out) {
+    const PC<double> pcd = pc_of(ph, double());
     double mass = 0, ke = 0, se = 0, umax = 0, pmin = 1e308, pmax = -1e308;
     double pin = 0, pout = 0, nin = 0, nout = 0, psum = 0, bad = 0;
-    const double inv_h = 1.0 / g.h, sh = 6.0 * ph.sigma;
+    const double inv_h = g.ih, sh = 6.0 * ph.sigma;
     for_cells(g, [&](int ci, int cj, int ck, int idx) {
         const Nb6 nb = nb6<DIM>(g, ci, cj, ck, idx);
         double pc = double(phi[idx]);
         int im[3] = {nb.m[0], nb.m[2], nb.m[4]};
         const T* uv[3] = {u0, u1, u2};
-        double rc = double(rho_of(T(pc), ph));
+        double rc = rho_of(pc, pcd);
         double grad2 = 0.0;
         for (int d = 0; d < DIM; ++d) {
             double pm = double(phi[im[d]]);
-            double rf = 0.5 * (rc + double(rho_of(T(pm), ph)));
+            double rf = 0.5 * (rc + rho_of(pm, pcd));
             double ud = double(uv[d][idx]);
             ke += 0.5 * rf * ud * ud;
             umax = fmax(umax, fabs(ud));
@@ -527,8 +540,8 @@ void launch_diagnostics(const Dims& g, const Phys& ph, const T* phi, const T* co
     template void launch_divergence<T, D>(const Dims&, const T* const*, double, double*,        \
                                           RedBuf, CGScalars*, cudaStream_t);                    \
     template void launch_correct<T, D>(const Dims&, const Phys&, const T*, const double* const*, \
-                                       const T* const*, const double*, double, T* const*,       \
-                                       cudaStream_t);                                           \
+                                       const float* const*, const T* const*, const double*,     \
+                                       double, T* const*, cudaStream_t);                        \
     template void launch_diagnostics<T, D>(const Dims&, const Phys&, const T*, const T* const*, \
                                            const double*, RedBuf, DiagOut*, cudaStream_t);
 

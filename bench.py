@@ -125,31 +125,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Algorithmic bytes per cell and launch of each kernel class (float32 fields,
-# float64 CG vectors; see the design doc for the derivation).
+# Algorithmic bytes per cell and launch of each kernel class on the mixed 3D
+# path (float32 fields and face coefficients, float64 pressure and divergence;
+# derivation in the design doc).
 def algo_bytes_per_cell(cls, dim, w):
     d = dim
     table = {
-        # red or black half sweep on the finest level: read x, f, phi, write half of x
-        "mg_gs_level0": 3 * w + 0.5 * w,
-        # p = z + beta p, q = A p, p.q: read z, p, phi; write p, q
-        "cg_dir_spmv": w + 8 + w + 8 + 8,
-        # x += a p, r -= a q, r.r: read p, q, x, r; write x, r, r32
-        "cg_update": 4 * 8 + 2 * 8 + (w if w == 4 else 0),
+        # one full red-black sweep, mean of the pre-smoothing sweep (zero start:
+        # read f and 3 face arrays, write x) and the post-smoothing sweep
+        # (read x, f, 3 face arrays, and q for the fused dots; write x)
+        "mg_gs_level0": 0.5 * ((1 + d + 1) * w + (1 + 1 + d + 1 + 1) * w),
+        # p = z + beta p, q = A p: read z, p, 3 face arrays; write p, q
+        "cg_dir_spmv": (2 + d + 2) * w,
+        # e += a p, r -= a q: read e, p, r, q; write e, r
+        "cg_update": 6 * w,
         # r.z, z.q: read z, r, q
-        "cg_dots": w + 16,
-        # stage kernel: read phi_s, u_s, phi_n, u_n, normals, aux, acc; write phi, u*, acc
-        "stage": (1 + d + 1 + d + d + 1 + (1 + d)) * w + (1 + d + 1 + d) * w,
+        "cg_dots": 3 * w,
+        # r = f - A x in float64: read x, b (float64), 3 face arrays; write r
+        "ir_residual_f64": 16 + d * w + w,
+        # stage kernel: read phi_s, u_s, phi^n, u^n, normals, mu, accumulators;
+        # write phi, u*, accumulators (stages 1-2; the first and last move less)
+        "stage": (1 + d + 1 + d + d + 1 + 1 + d) * w + (1 + d + 1 + d) * w,
         "cell_pass": w + (d + 1) * w,
-        "correct": (1 + d) * w + 8 + d * w,
+        "correct": d * w + 8 + d * w + d * w,
         "divergence": d * w + 8,
-        "mg_restrict": 3 * w + w / (2 ** d),
+        "mg_restrict": (2 + d) * w + w / (2 ** d),
         "mg_prolong": 2 * w + w / (2 ** d),
     }
     return table.get(cls)
 
 
-def cpu_sample_rate(p, steps=2, n=32):
+def cpu_sample_rate(p, steps=2, n=16):
     """The oracle (as it stands) on a bounded sample: `steps` RK4 steps of the same
     drop at n^d cells. Returns (Mcell-steps/s, cores, description)."""
     from oracle import pf_oracle as O
@@ -167,7 +173,8 @@ def cpu_sample_rate(p, steps=2, n=32):
         st = O.step(st, po)
     dt = time.perf_counter() - t0
     cells = n ** p["dim"]
-    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    # numpy elementwise stencils and SuperLU run on one core
+    cores = 1
     desc = (f"{steps} RK4 steps of the same drop at {n}^{p['dim']} (float64 numpy oracle with "
             f"a sparse direct pressure solve; the full {p['n'][0]}^{p['dim']} grid is out of "
             f"reach of the oracle)")
@@ -288,7 +295,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, sdesc = cpu_sample_rate(p, steps=2)
+        v, cores, sdesc = cpu_sample_rate(p, steps=6)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
 
     if rank == 0:

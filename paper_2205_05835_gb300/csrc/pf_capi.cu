@@ -278,7 +278,7 @@ struct ImplT final : Impl {
         if (DIM == 3 && sizeof(T) == sizeof(float))
             for (int l = 0; l < H.first_coarse; ++l)
                 H.lev[l].x2 = sweep3d_ok(H.lev[l].g) ? cv.take<T>(H.lev[l].g.ncell) : nullptr;
-        rb.part = cv.take<double>(kRedBlocks * 16);
+        rb.part = cv.take<double>(kRedPart);
         rb.counter = cv.take<unsigned int>(4);
         sc = cv.take<CGScalars>(1);
         gamma = cv.take<double>(1);
@@ -311,7 +311,7 @@ struct ImplT final : Impl {
             H.lev[l].f = cv.take<T>(m);
             for (int d = 0; d < 3; ++d) H.lev[l].beta[d] = d < DIM ? cv.take<T>(m) : nullptr;
         }
-        rb.part = cv.take<double>(kRedBlocks * 16);
+        rb.part = cv.take<double>(kRedPart);
         rb.counter = cv.take<unsigned int>(4);
         sc = cv.take<CGScalars>(1);
         dsum = cv.take<double>(4);
@@ -473,12 +473,29 @@ struct ImplT final : Impl {
             int cur = 0;
             for (int it = 0; it <= prm.poisson_maxit + poll_every; ++it) {
                 const int first = (it == 0);
-                io.z = launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof);
-                prof.begin(KC_CG_DOTS);
-                launch_in_dots<T, DIM>(g, io, first, rb, sc, st);
-                prof.end();
+                SweepDots sd;
+                sd.q = reinterpret_cast<const float*>(qT);
+                sd.rb = rb;
+                sd.sc = sc;
+                sd.first = first;
+                bool dots_done = false;
+                io.z = launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof, &sd, &dots_done);
+                if (!dots_done) {
+                    prof.begin(KC_CG_DOTS);
+                    launch_in_dots<T, DIM>(g, io, first, rb, sc, st);
+                    prof.end();
+                }
                 prof.begin(KC_CG_DIR);
-                launch_in_dir<T, DIM>(g, ph, io, cur, first, rb, sc, st);
+                if (DIM == 3 && sizeof(T) == sizeof(float) && beta32[0] != nullptr &&
+                    dir3d_ok(g)) {
+                    const float* bl[3] = {beta32[0], beta32[1], beta32[2]};
+                    launch_dir3d(g, reinterpret_cast<const float*>(io.z),
+                                 reinterpret_cast<const float*>(cur ? pd[1] : pd[0]),
+                                 reinterpret_cast<float*>(cur ? pd[0] : pd[1]),
+                                 reinterpret_cast<float*>(qT), bl, first, rb, sc, st);
+                } else {
+                    launch_in_dir<T, DIM>(g, ph, io, cur, first, rb, sc, st);
+                }
                 prof.end();
                 prof.begin(KC_CG_UPDATE);
                 launch_in_update<T, DIM>(g, io, cur, first, rb, sc, st);

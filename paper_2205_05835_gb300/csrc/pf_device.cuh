@@ -22,20 +22,30 @@ __device__ __forceinline__ Cell decode(int idx, const Dims& g) {
     return c;
 }
 
-// Wrapped neighbour index for offsets |o| <= 3 along each axis (n >= 4).
+// Wrapped neighbour index for offsets |o| <= 3 along each axis (n >= 4). Cells
+// at least 3 away from every periodic seam use plain offsets.
 template <int DIM>
 struct Nbr {
     int nx, ny, nz;
+    int idx, sz;
+    bool inner;
     int im[7], jm[7], km[7];   // wrapped coordinates for offsets -3..3
     __device__ __forceinline__ Nbr(const Cell& c, const Dims& g) : nx(g.nx), ny(g.ny), nz(g.nz) {
+        sz = g.nx * g.ny;
+        idx = (c.k * g.ny + c.j) * g.nx + c.i;
+        inner = c.i >= 3 && c.i < g.nx - 3 && c.j >= 3 && c.j < g.ny - 3 &&
+                (DIM == 2 || (c.k >= 3 && c.k < g.nz - 3));
+        if (!inner) {
 #pragma unroll
-        for (int o = -3; o <= 3; ++o) {
-            im[o + 3] = wrapi(c.i + o, g.nx);
-            jm[o + 3] = wrapi(c.j + o, g.ny);
-            km[o + 3] = (DIM == 3) ? wrapi(c.k + o, g.nz) : 0;
+            for (int o = -3; o <= 3; ++o) {
+                im[o + 3] = wrapi(c.i + o, g.nx);
+                jm[o + 3] = wrapi(c.j + o, g.ny);
+                km[o + 3] = (DIM == 3) ? wrapi(c.k + o, g.nz) : 0;
+            }
         }
     }
     __device__ __forceinline__ int at(int di, int dj, int dk) const {
+        if (inner) return idx + di + dj * nx + (DIM == 3 ? dk * sz : 0);
         return (km[dk + 3] * ny + jm[dj + 3]) * nx + im[di + 3];
     }
     // offset o along axis d
@@ -72,6 +82,46 @@ __device__ __forceinline__ float rho32(float phi, const Phys& ph) {
 }
 __device__ __forceinline__ float beta_face32(float pa, float pb, const Phys& ph) {
     return __frcp_rn(__fmul_rn(0.5f, __fadd_rn(rho32(pa, ph), rho32(pb, ph))));
+}
+
+// Double-float arithmetic (a value is an unevaluated sum hi + lo of two floats):
+// Knuth's TwoSum and the FMA form of Dekker's TwoProduct, both error free.
+struct f2 {
+    float hi, lo;
+};
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return f2{s, e};
+}
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return f2{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ f2 quick_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return f2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// (a.hi + a.lo) * (b.hi + b.lo), relative error about 2^-44
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return quick_two_sum(p.hi, p.lo);
+}
+
+// Double-well term c psi'(phi) = c phi (1 - phi) (1 - 2 phi) for a float32 phi:
+// 1 - phi and 1 - 2 phi are formed exactly as double-floats and multiplied with
+// error-free products, so the float32 result is the float64 evaluation rounded
+// to float32 (up to a rounding tie), without the float64 pipe. c is given as a
+// double-float (ch + cl).
+__device__ __forceinline__ float dwell32(float phi, float ch, float cl) {
+    const f2 a{phi, 0.f};
+    const f2 b = two_sum(1.f, -phi);
+    const f2 c = two_sum(1.f, -2.f * phi);   // 2 phi is exact
+    const f2 p = f2_mul(f2_mul(a, b), c);
+    const f2 q = f2_mul(p, f2{ch, cl});
+    return __fadd_rn(q.hi, q.lo);
 }
 
 // a / b: IEEE division in float64, multiplication by the correctly rounded
@@ -196,10 +246,10 @@ __device__ __forceinline__ void block_reduce_max(double (&v)[K], double* smem) {
 
 // Stores the block's K partials; returns true in every thread of the last
 // block to finish, after which `tot` holds the grid totals (fixed order).
-// Mode per value: 0 sum, 1 max.
+// Mode per value: 0 sum, 1 max. bid / nblocks: linear block index and count.
 template <int K>
-__device__ __forceinline__ bool grid_reduce(double (&v)[K], const int (&mode)[K], RedBuf rb,
-                                            double (&tot)[K]) {
+__device__ __forceinline__ bool grid_reduce_lin(double (&v)[K], const int (&mode)[K], RedBuf rb,
+                                                double (&tot)[K], int bid, int nblocks) {
     __shared__ double smem[K * 32];
     __shared__ bool last;
     double s[K], m[K];
@@ -212,10 +262,10 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], const int (&mode)[K]
     block_reduce_max<K>(m, smem);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q = 0; q < K; ++q) rb.part[blockIdx.x * K + q] = mode[q] == 0 ? s[q] : m[q];
+        for (int q = 0; q < K; ++q) rb.part[bid * K + q] = mode[q] == 0 ? s[q] : m[q];
         __threadfence();
         unsigned t = atomicAdd(rb.counter, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned)nblocks - 1);
     }
     __syncthreads();
     if (!last) return false;
@@ -225,7 +275,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], const int (&mode)[K]
         s[q] = 0.0;
         m[q] = -1.0e308;
     }
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
             double t = __ldcg(rb.part + b * K + q);
@@ -240,6 +290,12 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], const int (&mode)[K]
         *rb.counter = 0u;
     }
     return true;
+}
+
+template <int K>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], const int (&mode)[K], RedBuf rb,
+                                            double (&tot)[K]) {
+    return grid_reduce_lin<K>(v, mode, rb, tot, blockIdx.x, gridDim.x);
 }
 
 inline int red_grid(int n) {

@@ -120,11 +120,7 @@ struct MGLevel {
     T* x2;         // second correction buffer for out-of-place sweeps (nullptr: in place)
 };
 
-// One-pass red-black Gauss-Seidel sweep of a 3D float32 level (pf_mg3d.cu).
-bool sweep3d_ok(const Dims& g);
-void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
-                    float* xout, const MGLevel<float>* C, int first_color, const CGScalars* sc,
-                    cudaStream_t s);
+
 
 template <typename T>
 struct MGHier {
@@ -137,9 +133,29 @@ struct MGHier {
 
 // Reduction scratch: partial sums per block and a completion counter.
 struct RedBuf {
-    double* part;          // kRedBlocks * 8 doubles
+    double* part;          // kRedPart doubles (partials of up to kRedPart/2 blocks x 2 values)
     unsigned int* counter; // one counter, reset by the last block
 };
+constexpr int kRedPart = 1 << 17;
+
+// One-pass red-black Gauss-Seidel sweep of a 3D float32 level (pf_mg3d.cu).
+bool sweep3d_ok(const Dims& g);
+long long sweep3d_blocks(const Dims& g);   // CTAs of a tiled sweep / direction kernel
+// dots: also form r.z (r = the level's f, z = x_out) and z.q and set the CG
+// beta / rz scalars (the work of the CG dot kernel), first: no previous q.
+struct SweepDots {
+    const float* q;
+    RedBuf rb;
+    CGScalars* sc;
+    int first;
+};
+// Tiled CG direction update and operator product (3D float32, face arrays).
+bool dir3d_ok(const Dims& g);
+void launch_dir3d(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
+                  const float* const* beta, int first, RedBuf rb, CGScalars* sc, cudaStream_t s);
+void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
+                    float* xout, const SweepDots* dots, int first_color, const CGScalars* sc,
+                    cudaStream_t s);
 
 struct DiagOut {
     double mass, ke, se, umax, phi_min, phi_max;
@@ -227,10 +243,13 @@ void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* con
                      cudaStream_t s);
 template <typename T, int DIM>
 void launch_mg_setup(const Dims& g0, const Phys& ph, const T* phi, MGHier<T>& H, cudaStream_t s);
-// Runs one V-cycle; returns the level-0 buffer that holds the result.
+// Runs one V-cycle; returns the level-0 buffer that holds the result. With
+// dots != nullptr the last level-0 sweep may also perform the CG dot products
+// (then *dots_done is set).
 template <typename T, int DIM>
 T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc,
-                 cudaStream_t s, Prof* pr);
+                 cudaStream_t s, Prof* pr, const SweepDots* dots = nullptr,
+                 bool* dots_done = nullptr);
 template <typename T, int DIM>
 void launch_ir_residual(const Dims& g, const Phys& ph, const SolveIO<T, DIM>& io, int first,
                         RedBuf rb, CGScalars* sc, cudaStream_t s);

@@ -55,6 +55,11 @@ struct SweepArgs {
     float ih2;            // 1 / h^2
     int first_color;
     int zc;
+    int dots;             // also r.z and z.q (see SweepDots)
+    int first;
+    const float* q;
+    RedBuf rb;
+    CGScalars* scw;
 };
 
 // Copies run PD planes ahead. Rings (planes): x_in 3 + PD, f 4 + PD, rho 5 + PD
@@ -72,6 +77,7 @@ struct Smem {
 template <bool FROM_PHI>
 __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* smem_raw) {
     Smem<FROM_PHI>& S = *reinterpret_cast<Smem<FROM_PHI>*>(smem_raw);
+    float rz = 0.f, zq = 0.f;   // per-thread partial dots (A.dots)
 
     const Dims& g = A.g;
     const int tid = threadIdx.x;
@@ -199,11 +205,31 @@ __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* 
                 if (gj < g.ny && gi < g.nx) {
                     float* out = A.xout + kk * sz + gj * sy + gi;
                     *reinterpret_cast<float2*>(out) = make_float2(v_even, v_odd);
+                    if (A.dots) {
+                        const int sfb = slot<RF_>(kb);
+                        rz += S.f[sfb][b][ea + 2] * v_even + S.f[sfb][b][ea + 3] * v_odd;
+                        if (!A.first) {
+                            const float2 qq = __ldg(reinterpret_cast<const float2*>(
+                                A.q + (kk * sz + gj * sy + gi)));
+                            zq += v_even * qq.x + v_odd * qq.y;
+                        }
+                    }
                 }
             }
         }
     }
     cp_wait_all();
+    if (A.dots) {
+        double v[2] = {double(rz), double(zq)}, tot[2];
+        const int mode[2] = {0, 0};
+        const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        const int nb = gridDim.x * gridDim.y * gridDim.z;
+        if (grid_reduce_lin<2>(v, mode, A.rb, tot, bid, nb) && threadIdx.x == 0) {
+            CGScalars* sc = A.scw;
+            sc->beta = A.first ? 0.0 : -sc->alpha * tot[1] / sc->rz;
+            sc->rz = tot[0];
+        }
+    }
 }
 
 // finest level (coefficients from phi) and coarser levels (face arrays)
@@ -220,6 +246,20 @@ __global__ void __launch_bounds__(NT) k_sweep3d_coarse(SweepArgs A, const CGScal
 
 }  // namespace
 
+// z chunk of the tiled kernels: enough CTAs to fill the GPU (about 8 per SM),
+// 2..32 planes each
+static int tiled_zc(const Dims& g) {
+    const int cols = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    int zc = 32;
+    while (zc > 2 && (long long)cols * ((g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
+    return zc;
+}
+
+long long sweep3d_blocks(const Dims& g) {
+    const int zc = tiled_zc(g);
+    return (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * ((g.nz + zc - 1) / zc);
+}
+
 // Eligible: 3D float level with even sizes.
 bool sweep3d_ok(const Dims& g) {
     return g.nz > 1 && (g.nx % 2 == 0) && (g.ny % 2 == 0) && (g.nz % 2 == 0) && g.nx >= 4 &&
@@ -227,9 +267,8 @@ bool sweep3d_ok(const Dims& g) {
 }
 
 void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
-                    float* xout, const MGLevel<float>* C, int first_color, const CGScalars* sc,
+                    float* xout, const SweepDots* dots, int first_color, const CGScalars* sc,
                     cudaStream_t s) {
-    (void)C;
     static bool attr_set = false;
     if (!attr_set) {
         // dynamic shared memory beyond 48 KB, and a shared-memory carveout that
@@ -254,16 +293,173 @@ void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, c
     a.ph = ph;
     a.ih2 = L.g.ih2f;
     a.first_color = first_color;
-    // z chunk: enough CTAs to fill the GPU (about 8 per SM), 2..32 planes each
-    const int cols = ((L.g.nx + TX - 1) / TX) * ((L.g.ny + TY - 1) / TY);
-    int zc = 32;
-    while (zc > 2 && (long long)cols * ((L.g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
+    a.dots = dots != nullptr;
+    a.first = dots ? dots->first : 0;
+    a.q = dots ? dots->q : nullptr;
+    if (dots) {
+        a.rb = dots->rb;
+        a.scw = dots->sc;
+    } else {
+        a.rb = RedBuf{nullptr, nullptr};
+        a.scw = nullptr;
+    }
+    const int zc = tiled_zc(L.g);
     a.zc = zc;
     dim3 grid((L.g.nx + TX - 1) / TX, (L.g.ny + TY - 1) / TY, (L.g.nz + zc - 1) / zc);
+    if (dots && 2LL * grid.x * grid.y * grid.z > (long long)kRedPart) {
+        // more CTAs than reduction slots: the caller runs the dot kernel instead
+        a.dots = 0;
+    }
     if (L.beta[0] == nullptr)
         k_sweep3d_fine<<<grid, NT, sizeof(Smem<true>), s>>>(a, sc);
     else
         k_sweep3d_coarse<<<grid, NT, sizeof(Smem<false>), s>>>(a, sc);
+}
+
+}  // namespace pf
+
+// ---------------------------------------------------------------------------
+// CG search direction and operator product on 3D float32 grids, tiled:
+//   p_new = z + beta p_old ; q = A p_new ; alpha = rz / (p_new . q)
+// A CTA owns a 32 x 8 column tile and marches along z; z, p_old and the face
+// coefficients are copied into shared-memory rings by cp.async two planes
+// ahead, p_new of the neighbours is formed on the fly from them.
+// ---------------------------------------------------------------------------
+namespace pf {
+namespace {
+
+constexpr int DR = 5;     // ring planes (3 in use + 2 in flight)
+constexpr int DNT = 256;  // threads: one per tile column
+
+struct DirSmem {
+    float z[DR][HY][HX];
+    float p[DR][HY][HX];
+    float b[3][DR][HY][HX];
+};
+
+struct DirArgs {
+    Dims g;
+    const float* z;
+    const float* p_old;
+    float* p_new;
+    float* q;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    float ih2;
+    int first;
+    int zc;
+    RedBuf rb;
+    CGScalars* sc;
+};
+
+__global__ void __launch_bounds__(DNT) k_dir3d(DirArgs A) {
+    CGScalars* sc = A.sc;
+    if (sc->done || sc->idone) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DirSmem& S = *reinterpret_cast<DirSmem*>(smem_raw);
+    const Dims& g = A.g;
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * A.zc;
+    const int z1 = min(z0 + A.zc, g.nz);
+    const int sy = g.nx, sz = g.nx * g.ny;
+    const float bcg = A.first ? 0.f : float(sc->beta);
+    const bool has_pair = tid < NPAIR;
+    const int pb = tid / (HX / 2), pa = 2 * (tid - pb * (HX / 2));
+    const int poff = mod(j0 - 2 + pb, g.ny) * sy + mod(i0 - 2 + pa, g.nx);
+
+    auto issue = [&](int kp) {
+        if (has_pair && kp <= z1) {
+            const int gidx = mod(kp, g.nz) * sz + poff;
+            const int s = slot<DR>(kp);
+            cp_async8(&S.z[s][pb][pa], A.z + gidx);
+            if (!A.first) cp_async8(&S.p[s][pb][pa], A.p_old + gidx);
+            cp_async8(&S.b[0][s][pb][pa], A.bx + gidx);
+            cp_async8(&S.b[1][s][pb][pa], A.by + gidx);
+            cp_async8(&S.b[2][s][pb][pa], A.bz + gidx);
+        }
+        cp_commit();
+    };
+    auto pn = [&](int s, int b, int a) {
+        return A.first ? S.z[s][b][a] : S.z[s][b][a] + bcg * S.p[s][b][a];
+    };
+
+    // prologue: planes z0-1 .. z0+2; each step waits for plane k + 1 and keeps
+    // two planes in flight
+    issue(z0 - 1);
+    issue(z0);
+    issue(z0 + 1);
+    issue(z0 + 2);
+    float pq = 0.f;
+    const int ta = tid % TX, tb = tid / TX;
+    const int a = ta + 2, b = tb + 2;
+    const int gi = i0 + ta, gj = j0 + tb;
+    const bool own = gi < g.nx && gj < g.ny;
+    for (int k = z0; k < z1; ++k) {
+        cp_wait<1>();           // own copies up to plane k + 1 landed
+        __syncthreads();        // all copies of plane k + 1 visible; step k - 1 done
+        issue(k + 3);
+        const int s0 = slot<DR>(k), sm = slot<DR>(k - 1), sp = slot<DR>(k + 1);
+        const float pc = pn(s0, b, a);
+        float ax = S.b[0][s0][b][a] * (pc - pn(s0, b, a - 1)) +
+                   S.b[0][s0][b][a + 1] * (pc - pn(s0, b, a + 1)) +
+                   S.b[1][s0][b][a] * (pc - pn(s0, b - 1, a)) +
+                   S.b[1][s0][b + 1][a] * (pc - pn(s0, b + 1, a)) +
+                   S.b[2][s0][b][a] * (pc - pn(sm, b, a)) +
+                   S.b[2][sp][b][a] * (pc - pn(sp, b, a));
+        ax *= A.ih2;
+        if (own) {
+            const int idx = k * sz + gj * sy + gi;
+            A.p_new[idx] = pc;
+            A.q[idx] = ax;
+            pq += pc * ax;
+        }
+    }
+    cp_wait<0>();
+    double v[1] = {double(pq)}, tot[1];
+    const int mode[1] = {0};
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (grid_reduce_lin<1>(v, mode, A.rb, tot, bid, nb) && threadIdx.x == 0) {
+        sc->pq = tot[0];
+        sc->alpha = tot[0] != 0.0 ? sc->rz / tot[0] : 0.0;
+    }
+}
+
+}  // namespace
+
+bool dir3d_ok(const Dims& g) {
+    return g.nz > 1 && (g.nx % 2 == 0) && (g.ny % 2 == 0) && g.nx >= 4 && g.ny >= 4 &&
+           g.nz >= 4 && sweep3d_blocks(g) <= kRedPart;
+}
+
+void launch_dir3d(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
+                  const float* const* beta, int first, RedBuf rb, CGScalars* sc, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_dir3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(DirSmem));
+        cudaFuncSetAttribute(k_dir3d, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        attr_set = true;
+    }
+    DirArgs a;
+    a.g = g;
+    a.z = z;
+    a.p_old = p_old;
+    a.p_new = p_new;
+    a.q = q;
+    a.bx = beta[0];
+    a.by = beta[1];
+    a.bz = beta[2];
+    a.ih2 = g.ih2f;
+    a.first = first;
+    a.rb = rb;
+    a.sc = sc;
+    const int zc = tiled_zc(g);
+    a.zc = zc;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + zc - 1) / zc);
+    k_dir3d<<<grid, DNT, sizeof(DirSmem), s>>>(a);
 }
 
 }  // namespace pf

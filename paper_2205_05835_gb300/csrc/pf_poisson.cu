@@ -332,7 +332,8 @@ static bool tiled_level(const MGLevel<T>& L) {
 
 template <typename T, int DIM>
 T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc,
-                 cudaStream_t s, Prof* pr) {
+                 cudaStream_t s, Prof* pr, const SweepDots* dots, bool* dots_done) {
+    if (dots_done) *dots_done = false;
     const int l0 = H.first_coarse;
     T* fin[kMaxLevels];   // buffer holding each level's result
     for (int l = l0; l < H.nlev; ++l) fin[l] = H.lev[l].x;
@@ -391,12 +392,16 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                 k_prolong<T, DIM><<<row_grid(L.g, kThreads, 1 << 30), kThreads, 0, s>>>(Lp, C, sc);
                 pr->end();
                 for (int p = 0; p < H.post; ++p) {
+                    // the last level-0 sweep also forms the CG dot products
+                    const bool fuse = dots && l == 0 && p == H.post - 1 &&
+                                      2 * sweep3d_blocks(L.g) <= kRedPart;
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
                     launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
                                    reinterpret_cast<const float*>(phi), ph,
                                    reinterpret_cast<const float*>(cur), reinterpret_cast<float*>(oth),
-                                   nullptr, 1, sc, s);
+                                   fuse ? dots : nullptr, 1, sc, s);
                     pr->end();
+                    if (fuse && dots_done) *dots_done = true;
                     T* t = cur; cur = oth; oth = t;
                 }
                 fin[l] = cur;
@@ -456,17 +461,22 @@ __global__ void __launch_bounds__(kThreads)
 k_ir_residual(Dims g, Phys ph, SolveIO<T, DIM> io, int first, RedBuf rb, CGScalars* sc) {
     if (!first && sc->done) return;
     const double mb = sc->mean_b;
-    double ff = 0.0, rr = 0.0, rr32 = 0.0;
+    const bool pos = io.sign > 0.0;
+    // norms accumulate the rounded values per thread in T (a stopping test
+    // needs a few digits); the residual itself is formed in float64
+    T ff = T(0), rr = T(0);
     for_cells(g, [&](int i, int j, int k, int idx) {
-        const double f = io.sign * (io.b[idx] - mb);
+        const double f = pos ? io.b[idx] - mb : mb - io.b[idx];
         const double rv = f - apply_A64<T, DIM>(g, ph, io, io.x, i, j, k, idx);
         const T rt = T(rv);
         io.r[idx] = rt;
-        ff += f * f;
-        rr += rv * rv;
-        rr32 += double(rt) * double(rt);
+        if (first) {
+            const T ft = T(f);
+            ff += ft * ft;
+        }
+        rr += rt * rt;
     });
-    double v[3] = {ff, rr, rr32}, tot[3];
+    double v[3] = {double(ff), double(rr), double(rr)}, tot[3];
     const int mode[3] = {0, 0, 0};
     if (grid_reduce<3>(v, mode, rb, tot) && threadIdx.x == 0) {
         if (first) {
@@ -658,7 +668,7 @@ void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s) 
     template void launch_beta0<T, D>(const Dims&, const Phys&, const T*, double* const*,         \
                                      cudaStream_t);                                              \
     template T* launch_vcycle<T, D>(const Phys&, const T*, MGHier<T>&, const CGScalars*,         \
-                                    cudaStream_t, Prof*);                                        \
+                                    cudaStream_t, Prof*, const SweepDots*, bool*);               \
     template void launch_ir_residual<T, D>(const Dims&, const Phys&, const SolveIO<T, D>&, int,  \
                                            RedBuf, CGScalars*, cudaStream_t);                    \
     template void launch_ir_addcorr<T, D>(const Dims&, const SolveIO<T, D>&, CGScalars*,         \

@@ -119,6 +119,7 @@ k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* _
     const PC<T> pcn = pc_of(ph, T());
     const double sh = 6.0 * ph.sigma;
     const double c_dw = sh / ph.eps;         // (6 sigma / eps), float64 double-well factor
+    const float c_dw_hi = float(c_dw), c_dw_lo = float(c_dw - double(float(c_dw)));
     const T c_lap = T(sh * ph.eps);          // 6 sigma eps
     for_cells(g, [&](int ci, int cj, int ck, int idx) {
     Cell c{ci, cj, ck};
@@ -136,8 +137,15 @@ k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* _
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
             lap = lap + (ldg(phi, nb.ax(d, 1)) - T(2) * pc + ldg(phi, nb.ax(d, -1))) * inv_h2;
-        // double-well term psi'(phi) in float64 (cancellation near phi = 0, 1)
-        const T dw = T(c_dw * dpsi64(double(pc)));
+        // double-well term psi'(phi) in float64 precision (cancellation near
+        // phi = 0, 1): float64 arithmetic for the float64 path, error-free
+        // double-float products for the float32 path
+        T dw;
+        if constexpr (sizeof(T) == sizeof(double)) {
+            dw = T(c_dw * dpsi64(double(pc)));
+        } else {
+            dw = dwell32(float(pc), c_dw_hi, c_dw_lo);
+        }
         mu_out[idx] = dw - c_lap * lap;
     }
     if (kap_out) {
@@ -229,7 +237,9 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
         const T* kap = (ph.force == 0) ? io.aux + g.ncell : io.aux;
         T kc = ldg(kap, idx);
         T third = (ph.model == 1) ? eps * sqrt(g2) * kc : pc * (T(1) - pc) * kc;
-        T dp = T(dpsi64(double(pc)));
+        T dp;
+        if constexpr (sizeof(T) == sizeof(double)) dp = T(dpsi64(double(pc)));
+        else dp = dwell32(float(pc), 1.f, 0.f);
         kphi = kphi + gam * (eps * lap - divq(dp, eps) + third);
     }
 

@@ -220,6 +220,8 @@ def run_ours(args, rank, world, local_rank):
 
         dist.init_process_group("nccl")
     p, desc = workload(args.workload, args.n)
+    if args.inner_tol is not None:
+        p["inner_tol"] = args.inner_tol
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = pf.Simulation(p, stream=stream)
@@ -330,6 +332,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="osc384")
     ap.add_argument("--n", type=int, default=None, help="override the grid size (testing)")
+    ap.add_argument("--inner-tol", type=float, default=None,
+                    help="relative reduction of each float32 inner solve (mixed path)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

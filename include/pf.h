@@ -91,6 +91,8 @@ typedef struct {
                              R (1 + a P_n(cos theta)) [3D] */
     int mg_pre, mg_post;  /* red-black Gauss-Seidel sweeps before/after coarse correction (0: 1) */
     double bound_tol;     /* > 0: flag PF_ERR_UNBOUNDED when phi leaves [-tol, 1 + tol] */
+    double inner_tol;     /* mixed precision: relative residual reduction of each float32
+                             inner solve between float64 refinements (0: 1e-6) */
     int reserved[8];      /* must be zero */
 } pf_params;
 

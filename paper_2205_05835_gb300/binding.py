@@ -42,6 +42,7 @@ class pf_params(ctypes.Structure):
         ("R", ctypes.c_double), ("pert_mode", ctypes.c_int), ("pert_amp", ctypes.c_double),
         ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int),
         ("bound_tol", ctypes.c_double),
+        ("inner_tol", ctypes.c_double),
         ("reserved", ctypes.c_int * 8),
     ]
 

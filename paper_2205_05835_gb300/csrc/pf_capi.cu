@@ -130,6 +130,10 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "viscosities, sigma and delta_n must be non-negative";
         return PF_ERR_INVALID;
     }
+    if (p->inner_tol < 0 || p->inner_tol >= 1) {
+        why = "inner_tol must be in [0, 1)";
+        return PF_ERR_INVALID;
+    }
     if (!(p->poisson_rtol > 0) || p->poisson_maxit < 1) {
         why = "poisson_rtol must be > 0 and poisson_maxit >= 1";
         return PF_ERR_INVALID;
@@ -329,7 +333,7 @@ struct ImplT final : Impl {
         memset(&s0, 0, sizeof(s0));
         s0.rtol2 = prm.poisson_rtol * prm.poisson_rtol;
         s0.maxit = prm.poisson_maxit;
-        s0.eta2_min = sizeof(T) == sizeof(double) ? 0.0 : 1e-8;
+        s0.eta2_min = sizeof(T) == sizeof(double) ? 0.0 : inner_eta2();
         CK(cudaMemcpyAsync(sc, &s0, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
         launch_convert_in<T>(phi_in, phiN, (int)n, st);
         CK(cudaMemcpyAsync(b, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -354,6 +358,12 @@ struct ImplT final : Impl {
         CK(cudaGetLastError());
         h_sc = nullptr;
         return s;
+    }
+
+    // squared floor of the inner relative tolerance (mixed path)
+    double inner_eta2() const {
+        const double t = prm.inner_tol > 0 ? prm.inner_tol : 1e-6;
+        return t * t;
     }
 
     pf_status alloc_host() {
@@ -386,7 +396,7 @@ struct ImplT final : Impl {
         s0.maxit = prm.poisson_maxit;
         // inner relative tolerance floor: float32 inner solves gain ~4 digits per
         // outer step; float64 inner solves go straight to the final tolerance
-        s0.eta2_min = sizeof(T) == sizeof(double) ? 0.0 : 1e-8;
+        s0.eta2_min = sizeof(T) == sizeof(double) ? 0.0 : inner_eta2();
         *h_sc = s0;
         CK(cudaMemcpyAsync(sc, h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(gamma, 0, sizeof(double), st));

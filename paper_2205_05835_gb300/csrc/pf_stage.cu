@@ -393,10 +393,22 @@ k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T
             dv += (double(u1[nb.m[3]]) - double(u1[idx])) * inv_h;
             if (DIM == 3) dv += (double(u2[nb.m[5]]) - double(u2[idx])) * inv_h;
         } else {
-            // float32 velocities: the differences are exact in float64 and summed there
-            dv = (double(u0[nb.m[1]]) - double(u0[idx])) + (double(u1[nb.m[3]]) - double(u1[idx]));
-            if (DIM == 3) dv += double(u2[nb.m[5]]) - double(u2[idx]);
-            dv *= inv_h;
+            // float32 velocities: exact differences (TwoSum) summed as a
+            // double-float, converted once to float64
+            const float* uf0 = reinterpret_cast<const float*>(u0);
+            const float* uf1 = reinterpret_cast<const float*>(u1);
+            const float* uf2 = reinterpret_cast<const float*>(u2);
+            f2 a = two_sum(uf0[nb.m[1]], -uf0[idx]);
+            const f2 b1 = two_sum(uf1[nb.m[3]], -uf1[idx]);
+            f2 t = two_sum(a.hi, b1.hi);
+            t.lo = __fadd_rn(t.lo, __fadd_rn(a.lo, b1.lo));
+            if (DIM == 3) {
+                const f2 c1 = two_sum(uf2[nb.m[5]], -uf2[idx]);
+                f2 t2 = two_sum(t.hi, c1.hi);
+                t2.lo = __fadd_rn(t2.lo, __fadd_rn(t.lo, c1.lo));
+                t = t2;
+            }
+            dv = (double(t.hi) + double(t.lo)) * inv_h;
         }
         dv *= inv_tau;
         b[idx] = dv;
@@ -426,6 +438,7 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
           const T* __restrict__ s1, const T* __restrict__ s2, const double* __restrict__ p,
           double tau, T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2) {
     const double inv_h = g.ih;
+    const float tau_h = float(tau * g.ih);
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
         const double pp = p[idx];
@@ -442,10 +455,10 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
                 ov[d][idx] = T(double(sv[d][idx]) - tau * bv[d][idx] * gp);
             } else {
                 // float32 path: same beta as the pressure operator; the pressure
-                // difference is formed in float64, the update in float32
+                // difference is formed in float64, scaled and applied in float32
                 const float beta = f0 != nullptr ? __ldg(fv[d] + idx)
                                                  : beta_face32(float(phi[idx]), float(phi[m]), ph);
-                const float gp = float((pp - p[m]) * (tau * inv_h));
+                const float gp = float(pp - p[m]) * tau_h;
                 ov[d][idx] = T(float(sv[d][idx]) - beta * gp);
             }
         }

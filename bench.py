@@ -52,6 +52,13 @@ def workload(name, n=None):
     elif name == "drop256":
         p = I.static_drop_256_r1000(precision="mixed")
         desc = "2D static drop 256^2, rho ratio 1000, mu ratio 100, CDI + EB, mixed"
+    elif name == "batch256":
+        plist = I.batch_manifest(count=256)
+        cells = sum(q["n"][0] * q["n"][1] for q in plist)
+        desc = (f"256 2D drops, N ~ U{{64..512}} (seed {I.BATCH_SEED}), R in [0.15, 0.3], "
+                f"La log-uniform in [1e2, 1e5], rho ratio in {{1, 10, 1000}}, "
+                f"static or mode-2, FP64, {cells} cells in total")
+        return plist, desc
     elif name == "drop64":
         p = I.static_drop_64()
         desc = "2D static drop 64^2, FP64, CDI + EB, La = 12000"
@@ -208,6 +215,39 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local_rank):
+    """Throughput of the batched executor on the seeded 256-drop manifest (host
+    wall clock bracketed by device synchronisation: the instances run on 256
+    streams)."""
+    import torch
+
+    import paper_2205_05835_gb300 as pf
+
+    torch.cuda.set_device(local_rank)
+    plist, desc = workload(args.workload)
+    bat = pf.Batch(plist, nthreads=args.threads)
+    cells = sum(bat.cells)
+    bat.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    bat.step(args.steps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    bat.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": cells * world * args.steps / wall / 1e6, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "cells": cells, "threads": args.threads,
+                       "timing": "host wall clock between device synchronisations"},
+            "clocks": clk}), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -332,6 +372,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="osc384")
     ap.add_argument("--n", type=int, default=None, help="override the grid size (testing)")
+    ap.add_argument("--threads", type=int, default=16, help="host threads (batch workload)")
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="relative reduction of each float32 inner solve (mixed path)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -342,6 +383,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload.startswith("batch"):
+        run_batch(args, rank, world, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

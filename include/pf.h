@@ -210,6 +210,28 @@ int pf_profile_read(pf_ctx* ctx, pf_profile_entry* out, int max_entries, int res
 pf_status pf_poisson_solve_static(const pf_params* prm, const double* phi, const double* rhs,
                                   double* x, void* stream, int* iters, double* relres);
 
+/* Batched execution of many independent instances (uneven grid sizes and
+ * physical parameters, e.g. a set of drops for a convergence or parameter
+ * study). Each instance is a context on its own CUDA stream, carved from one
+ * caller-owned workspace (256-byte aligned, pf_batch_workspace_size bytes);
+ * pf_batch_step advances every instance by nsteps with a pool of nthreads
+ * host threads (0: 16) that hand out instances largest first and sleep in
+ * blocking waits, so the kernels of different instances overlap on the GPU.
+ * Each instance computes exactly what pf_step computes on its own context.
+ * The library creates (and pf_batch_destroy destroys) one stream per instance;
+ * it allocates no device memory. pf_batch_context gives the context of
+ * instance i for pf_get_field / pf_diagnostics (do not pf_destroy it). Returns
+ * the first failing instance's status; the text is in pf_batch_last_error. */
+typedef struct pf_batch pf_batch;
+pf_status pf_batch_workspace_size(const pf_params* prms, int count, size_t* bytes);
+pf_status pf_batch_init(const pf_params* prms, int count, void* workspace, size_t workspace_bytes,
+                        int nthreads, pf_batch** out);
+pf_status pf_batch_step(pf_batch* b, int nsteps);
+int pf_batch_size(const pf_batch* b);
+pf_ctx* pf_batch_context(pf_batch* b, int i);
+void pf_batch_destroy(pf_batch* b);
+const char* pf_batch_last_error(const pf_batch* b);
+
 /* Wait for all work of the context and return the latched device status. */
 pf_status pf_sync(pf_ctx* ctx);
 

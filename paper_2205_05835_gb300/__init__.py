@@ -11,7 +11,9 @@ from __future__ import annotations
 import numpy as np
 
 from . import binding as B
-from .binding import (PFError, pf_destroy, pf_diagnostics, pf_eval_rhs, pf_get_field,  # noqa: F401
+from .binding import (PFError, pf_batch_context, pf_batch_destroy, pf_batch_init,  # noqa: F401
+                      pf_batch_size, pf_batch_step, pf_batch_workspace_size,
+                      pf_destroy, pf_diagnostics, pf_eval_rhs, pf_get_field,
                       pf_get_state, pf_init, pf_last_error, pf_poisson_solve,
                       pf_profile_enable, pf_profile_read, pf_project,
                       pf_set_field, pf_set_state, pf_state_bytes, pf_step, pf_sync,
@@ -120,6 +122,50 @@ class Simulation:
         if getattr(self, "ctx", None) is not None:
             pf_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent instances advanced together (pf_batch_*); workspace
+    allocated with torch on the current device."""
+
+    def __init__(self, param_list, nthreads=0):
+        import torch
+
+        self.params = [dict(p) for p in param_list]
+        self.prms = [make_params(p) for p in param_list]
+        self.nbytes = pf_batch_workspace_size(self.prms)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=dev)
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.b = pf_batch_init(self.prms, base, self.nbytes, nthreads)
+        self.cells = [int(np.prod([p.n[d] for d in range(p.dim)])) for p in self.prms]
+
+    def __len__(self):
+        return len(self.prms)
+
+    def step(self, nsteps=1):
+        pf_batch_step(self.b, nsteps)
+
+    def field(self, i, name):
+        p = self.prms[i]
+        shape = tuple(reversed([p.n[d] for d in range(p.dim)]))
+        out = np.empty(self.cells[i], dtype=np.float64)
+        pf_get_field(pf_batch_context(self.b, i), FIELDS[name], out.ctypes.data)
+        return out.reshape(shape)
+
+    def diagnostics(self, i):
+        return pf_diagnostics(pf_batch_context(self.b, i))
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            pf_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

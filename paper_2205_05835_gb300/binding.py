@@ -25,7 +25,9 @@ PF_FIELD_PHI, PF_FIELD_U, PF_FIELD_V, PF_FIELD_W, PF_FIELD_P = 0, 1, 2, 3, 4
 SYMBOLS = ["pf_workspace_size", "pf_init", "pf_step", "pf_project", "pf_diagnostics",
            "pf_get_field", "pf_set_field", "pf_state_bytes", "pf_get_state", "pf_set_state",
            "pf_eval_rhs", "pf_poisson_solve", "pf_sync", "pf_destroy", "pf_last_error",
-           "pf_profile_enable", "pf_profile_read", "pf_poisson_solve_static"]
+           "pf_profile_enable", "pf_profile_read", "pf_poisson_solve_static",
+           "pf_batch_workspace_size", "pf_batch_init", "pf_batch_step", "pf_batch_size",
+           "pf_batch_context", "pf_batch_destroy", "pf_batch_last_error"]
 
 
 class pf_params(ctypes.Structure):
@@ -97,6 +99,13 @@ def _load():
         "pf_profile_enable": (i32, [vp, i32]),
         "pf_profile_read": (i32, [vp, P(pf_profile_entry), i32, i32]),
         "pf_poisson_solve_static": (i32, [P(pf_params), vp, vp, vp, vp, P(i32), P(f64)]),
+        "pf_batch_workspace_size": (i32, [P(pf_params), i32, P(sz)]),
+        "pf_batch_init": (i32, [P(pf_params), i32, vp, sz, i32, P(vp)]),
+        "pf_batch_step": (i32, [vp, i32]),
+        "pf_batch_size": (i32, [vp]),
+        "pf_batch_context": (vp, [vp, i32]),
+        "pf_batch_destroy": (None, [vp]),
+        "pf_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +213,49 @@ def pf_poisson_solve_static(params: pf_params, phi: int, rhs: int, x: int, strea
     if st not in (PF_OK, PF_ERR_NOT_CONVERGED):
         _check(st, None)
     return st, it.value, rel.value
+
+
+def _params_array(plist):
+    arr = (pf_params * len(plist))()
+    for i, p in enumerate(plist):
+        arr[i] = p
+    return arr
+
+
+def _check_batch(status, b=None):
+    if status != PF_OK:
+        msg = LIB.pf_batch_last_error(b)
+        raise PFError(status, msg.decode() if msg else "")
+    return status
+
+
+def pf_batch_workspace_size(plist) -> int:
+    n = ctypes.c_size_t(0)
+    _check_batch(LIB.pf_batch_workspace_size(_params_array(plist), len(plist), ctypes.byref(n)))
+    return n.value
+
+
+def pf_batch_init(plist, workspace: int, workspace_bytes: int, nthreads: int = 0):
+    b = ctypes.c_void_p(0)
+    _check_batch(LIB.pf_batch_init(_params_array(plist), len(plist), workspace, workspace_bytes,
+                                   nthreads, ctypes.byref(b)))
+    return b
+
+
+def pf_batch_step(b, nsteps: int):
+    return _check_batch(LIB.pf_batch_step(b, nsteps), b)
+
+
+def pf_batch_size(b) -> int:
+    return LIB.pf_batch_size(b)
+
+
+def pf_batch_context(b, i: int):
+    return ctypes.c_void_p(LIB.pf_batch_context(b, i))
+
+
+def pf_batch_destroy(b):
+    LIB.pf_batch_destroy(b)
 
 
 def pf_last_error(ctx=None) -> str:

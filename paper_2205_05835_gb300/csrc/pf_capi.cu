@@ -42,6 +42,7 @@ const double kRK4W[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
 
 struct Impl {
     virtual ~Impl() {}
+    virtual pf_status set_blocking(bool on) = 0;
     virtual void carve(Carver& cv) = 0;
     virtual void init_phi(const double* phi0) = 0;
     virtual void zero_state() = 0;
@@ -231,9 +232,11 @@ struct ImplT final : Impl {
     }
 
     bool owns_host = false;
+    cudaEvent_t sleep_ev = nullptr;   // blocking-sync event (batched execution)
 
     ~ImplT() override {
         prof.destroy();
+        if (sleep_ev) cudaEventDestroy(sleep_ev);
         if (!owns_host) return;
         if (h_sc) cudaFreeHost(h_sc);
         if (h_dout) cudaFreeHost(h_dout);
@@ -451,7 +454,13 @@ struct ImplT final : Impl {
 
     pf_status poll() {
         CK(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        if (sleep_ev) {
+            // the calling thread sleeps instead of spinning (many contexts per thread pool)
+            CK(cudaEventRecord(sleep_ev, st));
+            CK(cudaEventSynchronize(sleep_ev));
+        } else {
+            CK(cudaStreamSynchronize(st));
+        }
         prof.harvest();
         return PF_OK;
     }
@@ -805,6 +814,16 @@ struct ImplT final : Impl {
         CK(cudaGetLastError());
         return PF_OK;
     }
+
+    pf_status set_blocking(bool on) override {
+        if (on && !sleep_ev)
+            CK(cudaEventCreateWithFlags(&sleep_ev, cudaEventBlockingSync | cudaEventDisableTiming));
+        if (!on && sleep_ev) {
+            CK(cudaEventDestroy(sleep_ev));
+            sleep_ev = nullptr;
+        }
+        return PF_OK;
+    }
 };
 
 Impl* make_impl(const pf_params& p, cudaStream_t s, std::string& err) {
@@ -847,6 +866,13 @@ pf_status run_static_solve(const pf_params& prm, cudaStream_t st, void* scratch,
 }
 
 }  // namespace
+
+namespace pf {
+int ctx_set_blocking(pf_ctx* ctx, int on) {
+    if (!ctx) return PF_ERR_INVALID;
+    return (int)ctx->impl->set_blocking(on != 0);
+}
+}  // namespace pf
 
 extern "C" {
 

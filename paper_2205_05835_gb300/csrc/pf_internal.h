@@ -267,3 +267,9 @@ void launch_in_update(const Dims& g, const SolveIO<T, DIM>& io, int cur, int fir
 void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s);
 
 }  // namespace pf
+
+struct pf_ctx;
+namespace pf {
+// Make the context's host waits sleep on a blocking-sync event (pf_capi.cu).
+int ctx_set_blocking(pf_ctx* ctx, int on);
+}  // namespace pf

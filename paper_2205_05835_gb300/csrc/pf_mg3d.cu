@@ -14,6 +14,8 @@
 // reads another's output. Zero start (x_in = 0) skips the x_in copies.
 // Requires even nx, ny, nz (consistent periodic colouring); tiles may be
 // ragged (sizes need not be multiples of 32 x 8) since every index wraps.
+#include <mutex>
+
 #include "pf_device.cuh"
 
 namespace pf {
@@ -269,8 +271,8 @@ bool sweep3d_ok(const Dims& g) {
 void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
                     float* xout, const SweepDots* dots, int first_color, const CGScalars* sc,
                     cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
         // dynamic shared memory beyond 48 KB, and a shared-memory carveout that
         // lets several CTAs share an SM
         cudaFuncSetAttribute(k_sweep3d_fine, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -279,8 +281,7 @@ void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, c
                              (int)sizeof(Smem<false>));
         cudaFuncSetAttribute(k_sweep3d_fine, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaFuncSetAttribute(k_sweep3d_coarse, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        attr_set = true;
-    }
+    });
     SweepArgs a;
     a.g = L.g;
     a.xin = xin;
@@ -436,13 +437,12 @@ bool dir3d_ok(const Dims& g) {
 
 void launch_dir3d(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
                   const float* const* beta, int first, RedBuf rb, CGScalars* sc, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
         cudaFuncSetAttribute(k_dir3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(DirSmem));
         cudaFuncSetAttribute(k_dir3d, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        attr_set = true;
-    }
+    });
     DirArgs a;
     a.g = g;
     a.z = z;

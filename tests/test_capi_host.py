@@ -20,7 +20,7 @@ def pf():
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "pf.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:pf_status|void|size_t|int|const char\*)\s+(pf_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:pf_status|void|size_t|int|const char\*|pf_ctx\*)\s+(pf_\w+)\s*\(",
                                  src, flags=re.M)))
 
 
@@ -82,3 +82,32 @@ def test_init_rejects_bad_workspace_without_touching_the_gpu(pf):
     assert "workspace" in pf.pf_last_error(None)
     st = pf.B.LIB.pf_init(ctypes.byref(p), 0x1001, 1 << 40, None, None, ctypes.byref(ctx))
     assert st == pf.B.PF_ERR_WORKSPACE
+
+
+def test_batch_workspace_is_the_sum_of_aligned_instances(pf):
+    import pf_inputs as I
+
+    man = I.batch_manifest(count=5)
+    prms = [pf.make_params(p) for p in man]
+    total = pf.pf_batch_workspace_size(prms)
+    want = sum((pf.pf_workspace_size(q) + 255) // 256 * 256 for q in prms)
+    assert total == want
+    bad = [pf.make_params(p) for p in man]
+    bad[3].dim = 5
+    with pytest.raises(pf.PFError) as e:
+        pf.pf_batch_workspace_size(bad)
+    assert "instance 3" in str(e.value)
+
+
+def test_batch_manifest_is_seeded_and_in_range():
+    import pf_inputs as I
+
+    a = I.batch_manifest(count=256)
+    b = I.batch_manifest(count=256)
+    assert [p["n"] for p in a] == [p["n"] for p in b]
+    ns = [p["n"][0] for p in a]
+    assert min(ns) >= 64 and max(ns) <= 512 and all(n % 16 == 0 for n in ns)
+    assert all(0.15 <= p["R"] <= 0.3 for p in a)
+    assert {p["rho_in"] / p["rho_out"] for p in a} <= {1.0, 10.0, 1000.0}
+    cells = sum(n * n for n in ns)
+    assert 1.5e7 < cells < 3.5e7

@@ -52,12 +52,14 @@ def workload(name, n=None):
     elif name == "drop256":
         p = I.static_drop_256_r1000(precision="mixed")
         desc = "2D static drop 256^2, rho ratio 1000, mu ratio 100, CDI + EB, mixed"
-    elif name == "batch256":
-        plist = I.batch_manifest(count=256)
+    elif name in ("batch256", "batch256_fp64"):
+        prec = "fp64" if name.endswith("fp64") else "mixed"
+        plist = I.batch_manifest(count=256, precision=prec,
+                                 poisson_rtol=1e-12 if prec == "fp64" else 1e-10)
         cells = sum(q["n"][0] * q["n"][1] for q in plist)
         desc = (f"256 2D drops, N ~ U{{64..512}} (seed {I.BATCH_SEED}), R in [0.15, 0.3], "
                 f"La log-uniform in [1e2, 1e5], rho ratio in {{1, 10, 1000}}, "
-                f"static or mode-2, FP64, {cells} cells in total")
+                f"static or mode-2, {prec}, {cells} cells in total")
         return plist, desc
     elif name == "drop64":
         p = I.static_drop_64()
@@ -242,7 +244,8 @@ def run_batch(args, rank, world, local_rank):
             "metric": METRIC, "value": cells * world * args.steps / wall / 1e6, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if "fp64" in args.workload else "f32+f64",
+            "data": "synthetic",
             "config": {"workload": desc, "cells": cells, "threads": args.threads,
                        "timing": "host wall clock between device synchronisations"},
             "clocks": clk}), flush=True)

@@ -227,6 +227,8 @@ pf_status pf_batch_workspace_size(const pf_params* prms, int count, size_t* byte
 pf_status pf_batch_init(const pf_params* prms, int count, void* workspace, size_t workspace_bytes,
                         int nthreads, pf_batch** out);
 pf_status pf_batch_step(pf_batch* b, int nsteps);
+/* Instance i advances nsteps[i] steps (0: left as is); same execution model. */
+pf_status pf_batch_step_each(pf_batch* b, const int* nsteps);
 int pf_batch_size(const pf_batch* b);
 pf_ctx* pf_batch_context(pf_batch* b, int i);
 void pf_batch_destroy(pf_batch* b);

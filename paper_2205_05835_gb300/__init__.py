@@ -152,6 +152,10 @@ class Batch:
     def step(self, nsteps=1):
         pf_batch_step(self.b, nsteps)
 
+    def step_each(self, nsteps):
+        """Instance i advances nsteps[i] steps."""
+        B.pf_batch_step_each(self.b, nsteps)
+
     def field(self, i, name):
         p = self.prms[i]
         shape = tuple(reversed([p.n[d] for d in range(p.dim)]))

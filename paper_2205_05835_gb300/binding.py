@@ -26,7 +26,8 @@ SYMBOLS = ["pf_workspace_size", "pf_init", "pf_step", "pf_project", "pf_diagnost
            "pf_get_field", "pf_set_field", "pf_state_bytes", "pf_get_state", "pf_set_state",
            "pf_eval_rhs", "pf_poisson_solve", "pf_sync", "pf_destroy", "pf_last_error",
            "pf_profile_enable", "pf_profile_read", "pf_poisson_solve_static",
-           "pf_batch_workspace_size", "pf_batch_init", "pf_batch_step", "pf_batch_size",
+           "pf_batch_workspace_size", "pf_batch_init", "pf_batch_step", "pf_batch_step_each",
+           "pf_batch_size",
            "pf_batch_context", "pf_batch_destroy", "pf_batch_last_error"]
 
 
@@ -102,6 +103,7 @@ def _load():
         "pf_batch_workspace_size": (i32, [P(pf_params), i32, P(sz)]),
         "pf_batch_init": (i32, [P(pf_params), i32, vp, sz, i32, P(vp)]),
         "pf_batch_step": (i32, [vp, i32]),
+        "pf_batch_step_each": (i32, [vp, P(i32)]),
         "pf_batch_size": (i32, [vp]),
         "pf_batch_context": (vp, [vp, i32]),
         "pf_batch_destroy": (None, [vp]),
@@ -244,6 +246,11 @@ def pf_batch_init(plist, workspace: int, workspace_bytes: int, nthreads: int = 0
 
 def pf_batch_step(b, nsteps: int):
     return _check_batch(LIB.pf_batch_step(b, nsteps), b)
+
+
+def pf_batch_step_each(b, nsteps):
+    arr = (ctypes.c_int * len(nsteps))(*[int(v) for v in nsteps])
+    return _check_batch(LIB.pf_batch_step_each(b, arr), b)
 
 
 def pf_batch_size(b) -> int:

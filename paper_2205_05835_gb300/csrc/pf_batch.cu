@@ -40,6 +40,10 @@ long long cells_of(const pf_params& p) {
 }  // namespace
 
 extern "C" {
+pf_status pf_batch_step(pf_batch* b, int nsteps);
+}
+
+extern "C" {
 
 pf_status pf_batch_workspace_size(const pf_params* prms, int count, size_t* bytes) {
     if (!prms || count < 1 || !bytes) {
@@ -105,8 +109,7 @@ pf_status pf_batch_init(const pf_params* prms, int count, void* workspace, size_
     return PF_OK;
 }
 
-pf_status pf_batch_step(pf_batch* b, int nsteps) {
-    if (!b || nsteps < 0) return PF_ERR_INVALID;
+static pf_status batch_run(pf_batch* b, int nsteps, const int* each) {
     const int count = (int)b->ctx.size();
     std::atomic<int> next(0);
     std::atomic<int> status((int)PF_OK);
@@ -119,7 +122,9 @@ pf_status pf_batch_step(pf_batch* b, int nsteps) {
             const int t = next.fetch_add(1);
             if (t >= count) break;
             const int i = b->order[t];
-            pf_status s = pf_step(b->ctx[i], nsteps);
+            const int k = each ? each[i] : nsteps;
+            if (k <= 0) continue;
+            pf_status s = pf_step(b->ctx[i], k);
             if (s != PF_OK) {
                 int expect = (int)PF_OK;
                 if (status.compare_exchange_strong(expect, (int)s)) failed.store(i);
@@ -138,6 +143,18 @@ pf_status pf_batch_step(pf_batch* b, int nsteps) {
     }
     b->err.clear();
     return PF_OK;
+}
+
+pf_status pf_batch_step(pf_batch* b, int nsteps) {
+    if (!b || nsteps < 0) return PF_ERR_INVALID;
+    return batch_run(b, nsteps, nullptr);
+}
+
+pf_status pf_batch_step_each(pf_batch* b, const int* nsteps) {
+    if (!b || !nsteps) return PF_ERR_INVALID;
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+        if (nsteps[i] < 0) return PF_ERR_INVALID;
+    return batch_run(b, 0, nsteps);
 }
 
 int pf_batch_size(const pf_batch* b) { return b ? (int)b->ctx.size() : 0; }

@@ -508,7 +508,7 @@ struct ImplT final : Impl {
                 if (DIM == 3 && sizeof(T) == sizeof(float) && beta32[0] != nullptr &&
                     dir3d_ok(g)) {
                     const float* bl[3] = {beta32[0], beta32[1], beta32[2]};
-                    launch_dir3d(g, reinterpret_cast<const float*>(io.z),
+                    launch_dir3d_reg(g, reinterpret_cast<const float*>(io.z),
                                  reinterpret_cast<const float*>(cur ? pd[1] : pd[0]),
                                  reinterpret_cast<float*>(cur ? pd[0] : pd[1]),
                                  reinterpret_cast<float*>(qT), bl, first, rb, sc, st);

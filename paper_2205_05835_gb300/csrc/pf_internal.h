@@ -153,6 +153,9 @@ struct SweepDots {
 bool dir3d_ok(const Dims& g);
 void launch_dir3d(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
                   const float* const* beta, int first, RedBuf rb, CGScalars* sc, cudaStream_t s);
+void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
+                      const float* const* beta, int first, RedBuf rb, CGScalars* sc,
+                      cudaStream_t s);
 void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
                     float* xout, const SweepDots* dots, int first_color, const CGScalars* sc,
                     cudaStream_t s);

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(NT) k_sweep3d_coarse(SweepArgs A, const CGScal
 
 // z chunk of the tiled kernels: enough CTAs to fill the GPU (about 8 per SM),
 // 2..32 planes each
-static int tiled_zc(const Dims& g) {
+int tiled_zc(const Dims& g) {
     const int cols = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int zc = 32;
     while (zc > 2 && (long long)cols * ((g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
@@ -460,6 +460,112 @@ void launch_dir3d(const Dims& g, const float* z, const float* p_old, float* p_ne
     a.zc = zc;
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + zc - 1) / zc);
     k_dir3d<<<grid, DNT, sizeof(DirSmem), s>>>(a);
+}
+
+}  // namespace pf
+
+// ---------------------------------------------------------------------------
+// Register z-marching variant of the CG direction kernel: one thread per
+// column of a 32 x 8 tile; p_new of the column at k-1, k, k+1 and the z-face
+// coefficient above are carried in registers, the in-plane neighbours come
+// through L1. No shared memory and no barriers.
+// ---------------------------------------------------------------------------
+namespace pf {
+namespace {
+
+struct DirRegArgs {
+    Dims g;
+    const float* z;
+    const float* p_old;
+    float* p_new;
+    float* q;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    float ih2;
+    int first;
+    int zc;
+    RedBuf rb;
+    CGScalars* sc;
+};
+
+__global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
+    CGScalars* sc = A.sc;
+    if (sc->done || sc->idone) return;
+    const Dims& g = A.g;
+    const float bcg = A.first ? 0.f : float(sc->beta);
+    const int i = blockIdx.x * 32 + threadIdx.x % 32;
+    const int j = blockIdx.y * 8 + threadIdx.x / 32;
+    const int z0 = blockIdx.z * A.zc;
+    const int z1 = min(z0 + A.zc, g.nz);
+    float pq = 0.f;
+    if (i < g.nx && j < g.ny) {
+        const int sy = g.nx, sz = g.nx * g.ny;
+        const int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
+        const int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
+        const int col = j * sy + i;
+        const int ox_m = im - i, ox_p = ip - i, oy_m = (jm - j) * sy, oy_p = (jp - j) * sy;
+        auto pn = [&](int idx) {
+            const float zv = __ldg(A.z + idx);
+            return A.first ? zv : zv + bcg * __ldg(A.p_old + idx);
+        };
+        const int km1 = z0 == 0 ? g.nz - 1 : z0 - 1;
+        float p_m = pn(km1 * sz + col);
+        float p_c = pn(z0 * sz + col);
+        float bz_c = __ldg(A.bz + z0 * sz + col);
+#pragma unroll 2
+        for (int k = z0; k < z1; ++k) {
+            const int kp = k + 1 == g.nz ? 0 : k + 1;
+            const int idx = k * sz + col;
+            const int idxp = kp * sz + col;
+            const float p_p = pn(idxp);
+            const float bz_p = __ldg(A.bz + idxp);
+            const float ax = __ldg(A.bx + idx) * (p_c - pn(idx + ox_m)) +
+                             __ldg(A.bx + idx + ox_p) * (p_c - pn(idx + ox_p)) +
+                             __ldg(A.by + idx) * (p_c - pn(idx + oy_m)) +
+                             __ldg(A.by + idx + oy_p) * (p_c - pn(idx + oy_p)) +
+                             bz_c * (p_c - p_m) + bz_p * (p_c - p_p);
+            const float qv = ax * A.ih2;
+            A.p_new[idx] = p_c;
+            A.q[idx] = qv;
+            pq += p_c * qv;
+            p_m = p_c;
+            p_c = p_p;
+            bz_c = bz_p;
+        }
+    }
+    double v[1] = {double(pq)}, tot[1];
+    const int mode[1] = {0};
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (grid_reduce_lin<1>(v, mode, A.rb, tot, bid, nb) && threadIdx.x == 0) {
+        sc->pq = tot[0];
+        sc->alpha = tot[0] != 0.0 ? sc->rz / tot[0] : 0.0;
+    }
+}
+
+}  // namespace
+
+void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
+                      const float* const* beta, int first, RedBuf rb, CGScalars* sc,
+                      cudaStream_t s) {
+    DirRegArgs a;
+    a.g = g;
+    a.z = z;
+    a.p_old = p_old;
+    a.p_new = p_new;
+    a.q = q;
+    a.bx = beta[0];
+    a.by = beta[1];
+    a.bz = beta[2];
+    a.ih2 = g.ih2f;
+    a.first = first;
+    a.rb = rb;
+    a.sc = sc;
+    const int zc = tiled_zc(g);
+    a.zc = zc;
+    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
+    k_dir3d_reg<<<grid, 256, 0, s>>>(a);
 }
 
 }  // namespace pf

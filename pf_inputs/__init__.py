@@ -104,7 +104,7 @@ def oscillating_drop_2d_256():
                           steps=500))
 
 
-def batch_manifest(count=256, seed=BATCH_SEED):
+def batch_manifest(count=256, seed=BATCH_SEED, precision="mixed", poisson_rtol=1e-10):
     """Seeded manifest of 2D drops of uneven sizes and Laplace numbers.
 
     N ~ U{64, 80, ..., 512}, R ~ U[0.15, 0.3], log10 La ~ U[2, 5],
@@ -124,7 +124,8 @@ def batch_manifest(count=256, seed=BATCH_SEED):
         out.append(finalize(_base(dim=2, n=(n, n, 1), R=R, rho_in=rho_in,
                                   rho_out=rho_in / ratio, mu_in=mu, mu_out=mu,
                                   pert_mode=2 if osc else 0,
-                                  pert_amp=0.05 if osc else 0.0, steps=1000)))
+                                  pert_amp=0.05 if osc else 0.0, steps=1000,
+                                  precision=precision, poisson_rtol=poisson_rtol)))
     return out
 
 

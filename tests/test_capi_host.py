@@ -111,3 +111,20 @@ def test_batch_manifest_is_seeded_and_in_range():
     assert {p["rho_in"] / p["rho_out"] for p in a} <= {1.0, 10.0, 1000.0}
     cells = sum(n * n for n in ns)
     assert 1.5e7 < cells < 3.5e7
+
+
+def test_study_instances_follow_section_3_1():
+    """Static-drop study instances: La = 12000 with D = 0.4, rho = 300; the
+    sharp-interface panel ties eps to the mesh by dx = sqrt(32) eps^(3/2)."""
+    import math
+
+    from paper_2205_05835_gb300 import studies as S
+
+    plist, keys = S.study_instances("eps", (32, 64, 128), ("cdi", "sb"), ("eb", "csf", "lcsf"))
+    assert len(plist) == 2 * 3 * 3 and keys[0] == ("cdi", "eb", 32)
+    for p, (m, f, n) in zip(plist, keys):
+        assert p["model"] == m and p["force"] == f and p["n"] == (n, n, 1)
+        assert abs(p["sigma"] * p["rho_in"] * 2 * p["R"] / p["mu_in"] ** 2 - 12000) < 1e-9
+        assert p["rho_in"] == p["rho_out"] == 300 and 2 * p["R"] == 0.4
+        assert abs(math.sqrt(32) * p["eps"] ** 1.5 - 1.0 / n) < 1e-12
+    assert abs(S.eps_of("eps", 32) - 1 / 32) < 1e-15 and S.eps_of("h", 256) == 1 / 32

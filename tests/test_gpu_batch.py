@@ -52,11 +52,28 @@ def test_batch_equals_individual_contexts(pf):
 def test_manifest_batch_runs(pf):
     """The seeded manifest of uneven drops (first 24 instances): finite, CDI mass
     conserved to float64/float32 rounding."""
-    plist = I.batch_manifest(count=24)
+    plist = I.batch_manifest(count=24, precision="fp64", poisson_rtol=1e-11)
     bat = pf.Batch(plist)
     m0 = [bat.diagnostics(i)["mass"] for i in range(len(bat))]
     bat.step(2)
     for i in range(len(bat)):
         d = bat.diagnostics(i)
         assert np.isfinite(d["ke"]) and abs(d["mass"] - m0[i]) <= 1e-9 * m0[i]
+    bat.close()
+
+
+def test_step_each_matches_individual_step_counts(pf):
+    """pf_batch_step_each: instance i advances exactly nsteps[i] steps."""
+    plist = instances()[:4]
+    counts = [2, 0, 3, 1]
+    bat = pf.Batch(plist, nthreads=2)
+    bat.step_each(counts)
+    for i, p in enumerate(plist):
+        sim = pf.Simulation(p)
+        if counts[i]:
+            sim.step(counts[i])
+        assert bat.diagnostics(i)["step"] == counts[i]
+        for name in ("phi", "u", "p"):
+            np.testing.assert_array_equal(bat.field(i, name), sim.field(name))
+        sim.close()
     bat.close()

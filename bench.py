@@ -140,18 +140,19 @@ class ClockSampler:
 def algo_bytes_per_cell(cls, dim, w):
     d = dim
     table = {
-        # one full red-black sweep, mean of the pre-smoothing sweep (zero start:
-        # read f and 3 face arrays, write x) and the post-smoothing sweep
-        # (read x, f, 3 face arrays, and q for the fused dots; write x)
-        "mg_gs_level0": 0.5 * ((1 + d + 1) * w + (1 + 1 + d + 1 + 1) * w),
+        # one full red-black sweep of the finest level (weights from phi), mean
+        # of the pre-smoothing sweep (zero start: read f, phi; write x) and the
+        # post-smoothing sweep (read x, f, phi, and q for the fused dots; write x)
+        "mg_gs_level0": 0.5 * (3 * w + 5 * w),
         # p = z + beta p, q = A p: read z, p, 3 face arrays; write p, q
         "cg_dir_spmv": (2 + d + 2) * w,
         # e += a p, r -= a q: read e, p, r, q; write e, r
         "cg_update": 6 * w,
         # r.z, z.q: read z, r, q
         "cg_dots": 3 * w,
-        # r = f - A x in float64: read x, b (float64), 3 face arrays; write r
-        "ir_residual_f64": 16 + d * w + w,
+        # r = f - A x in float64 (mixed: expanded form): read x, b, the float64
+        # copies of the d face arrays and their per-cell sum; write r
+        "ir_residual_f64": 16 + 8 * d + 8 + w if w == 4 else 16 + d * w + w,
         # stage kernel: read phi_s, u_s, phi^n, u^n, normals, mu, accumulators;
         # write phi, u*, accumulators (stages 1-2; the first and last move less)
         "stage": (1 + d + 1 + d + d + 1 + 1 + d) * w + (1 + d + 1 + d) * w,

@@ -149,13 +149,13 @@ struct SweepDots {
     CGScalars* sc;
     int first;
 };
-// Tiled CG direction update and operator product (3D float32, face arrays).
+// CG direction update and operator product (3D float32, face arrays).
 bool dir3d_ok(const Dims& g);
-void launch_dir3d(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
-                  const float* const* beta, int first, RedBuf rb, CGScalars* sc, cudaStream_t s);
 void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
                       const float* const* beta, int first, RedBuf rb, CGScalars* sc,
                       cudaStream_t s);
+// phi != nullptr: finest level, smoother weights from rho(phi); else the
+// level's face coefficient arrays
 void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
                     float* xout, const SweepDots* dots, int first_color, const CGScalars* sc,
                     cudaStream_t s);
@@ -228,6 +228,11 @@ struct SolveIO {
     const T* phi;          // phase field defining rho
     const double* beta64[3];  // float64 face coefficients (T = double), else nullptr
     const float* beta32[3];   // float32 face coefficients (T = float), else nullptr
+    // optional (mixed path): beta32 widened to float64 and, per cell, the sum of
+    // its 2 DIM face coefficients; with them the float64 residual takes the
+    // expanded form x_c sum_q beta_q - sum_q beta_q x_q
+    const double* wide[3];
+    const double* diag;
     const double* b;       // right-hand side (mean removed on the fly, times sign)
     double sign;
     double* x;             // float64 solution (warm start)
@@ -243,6 +248,7 @@ void launch_beta0(const Dims& g, const Phys& ph, const T* phi, double* const* be
                   cudaStream_t s);
 template <int DIM>
 void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
+                     double* const* wide, double* diag,
                      cudaStream_t s);
 template <typename T, int DIM>
 void launch_mg_setup(const Dims& g0, const Phys& ph, const T* phi, MGHier<T>& H, cudaStream_t s);

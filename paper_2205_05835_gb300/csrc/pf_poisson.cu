@@ -248,30 +248,51 @@ k_beta0(Dims g, Phys ph, const T* __restrict__ phi, double* __restrict__ b0,
 }
 
 // float32 face coefficients of the mixed path (the same beta_face32 as every
-// kernel that evaluates them from phi)
+// kernel that evaluates them from phi); optionally their float64 copies and
+// the per-cell sum of the 2 DIM coefficients of the cell. The plus-face
+// coefficient is recomputed here with the same operations (IEEE addition is
+// commutative), so the sum is over exactly the stored values; every float32
+// coefficient is exact in float64 and their sum is exact as long as the
+// coefficients span fewer than 2^26 in magnitude (density ratios far beyond
+// any in use), so the sum does not depend on the order of the additions.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_beta0_32(Dims g, Phys ph, const float* __restrict__ phi, float* __restrict__ b0,
-           float* __restrict__ b1, float* __restrict__ b2) {
+           float* __restrict__ b1, float* __restrict__ b2, double* __restrict__ w0,
+           double* __restrict__ w1, double* __restrict__ w2, double* __restrict__ dg) {
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
         const float pc = __ldg(phi + idx);
-        b0[idx] = beta_face32(pc, __ldg(phi + nb.m[0]), ph);
-        b1[idx] = beta_face32(pc, __ldg(phi + nb.m[2]), ph);
-        if (DIM == 3) b2[idx] = beta_face32(pc, __ldg(phi + nb.m[4]), ph);
+        const float m0 = beta_face32(pc, __ldg(phi + nb.m[0]), ph);
+        const float m1 = beta_face32(pc, __ldg(phi + nb.m[2]), ph);
+        const float m2 = DIM == 3 ? beta_face32(pc, __ldg(phi + nb.m[4]), ph) : 0.f;
+        b0[idx] = m0;
+        b1[idx] = m1;
+        if (DIM == 3) b2[idx] = m2;
+        if (dg != nullptr) {
+            w0[idx] = double(m0);
+            w1[idx] = double(m1);
+            if (DIM == 3) w2[idx] = double(m2);
+            double s = double(m0) + double(beta_face32(pc, __ldg(phi + nb.m[1]), ph));
+            s += double(m1) + double(beta_face32(pc, __ldg(phi + nb.m[3]), ph));
+            if (DIM == 3) s += double(m2) + double(beta_face32(pc, __ldg(phi + nb.m[5]), ph));
+            dg[idx] = s;
+        }
     });
 }
 
 template <int DIM>
 void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
-                     cudaStream_t s) {
+                     double* const* wide, double* diag, cudaStream_t s) {
     k_beta0_32<DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
-        g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1]);
+        g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1],
+        diag ? wide[0] : nullptr, diag ? wide[1] : nullptr,
+        diag ? (DIM == 3 ? wide[2] : wide[1]) : nullptr, diag);
 }
 template void launch_beta0_32<2>(const Dims&, const Phys&, const float*, float* const*,
-                                 cudaStream_t);
+                                 double* const*, double*, cudaStream_t);
 template void launch_beta0_32<3>(const Dims&, const Phys&, const float*, float* const*,
-                                 cudaStream_t);
+                                 double* const*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // single-CTA kernel for all levels >= first_coarse
@@ -401,7 +422,7 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                 for (int p = 0; p < H.pre; ++p) {
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
                     launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
-                                   reinterpret_cast<const float*>(phi), ph,
+                                   l == 0 ? reinterpret_cast<const float*>(phi) : nullptr, ph,
                                    p == 0 ? nullptr : reinterpret_cast<const float*>(b),
                                    reinterpret_cast<float*>(p == 0 ? a : (p % 2 ? b : a)), nullptr,
                                    0, sc, s);
@@ -447,7 +468,7 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                                       2 * sweep3d_blocks(L.g) <= kRedPart;
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
                     launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
-                                   reinterpret_cast<const float*>(phi), ph,
+                                   l == 0 ? reinterpret_cast<const float*>(phi) : nullptr, ph,
                                    reinterpret_cast<const float*>(cur), reinterpret_cast<float*>(oth),
                                    fuse ? dots : nullptr, 1, sc, s);
                     pr->end();
@@ -517,7 +538,28 @@ k_ir_residual(Dims g, Phys ph, SolveIO<T, DIM> io, int first, RedBuf rb, CGScala
     T ff = T(0), rr = T(0);
     for_cells(g, [&](int i, int j, int k, int idx) {
         const double f = pos ? io.b[idx] - mb : mb - io.b[idx];
-        const double rv = f - apply_A64<T, DIM>(g, ph, io, io.x, i, j, k, idx);
+        double rv;
+        if (io.diag != nullptr) {
+            // the same operator as x_c sum_q beta_q - sum_q beta_q x_q (the sum
+            // is exact): one multiply-add per face instead of a subtraction and
+            // a conversion and a multiply-add. Its cancellation leaves a rounding
+            // error of a few units in the last place of |x| sum_q beta_q,
+            // relative to ||f|| at most about 2.5e-17 N^2 (a smooth solution);
+            // the context selects this form only for tolerances well above that.
+            const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
+            const double* __restrict__ x = io.x;
+            double s = io.wide[0][idx] * x[nb.m[0]];
+            s = fma(io.wide[0][nb.m[1]], x[nb.m[1]], s);
+            s = fma(io.wide[1][idx], x[nb.m[2]], s);
+            s = fma(io.wide[1][nb.m[3]], x[nb.m[3]], s);
+            if (DIM == 3) {
+                s = fma(io.wide[2][idx], x[nb.m[4]], s);
+                s = fma(io.wide[2][nb.m[5]], x[nb.m[5]], s);
+            }
+            rv = fma(-g.ih2, fma(x[idx], io.diag[idx], -s), f);
+        } else {
+            rv = f - apply_A64<T, DIM>(g, ph, io, io.x, i, j, k, idx);
+        }
         const T rt = T(rv);
         io.r[idx] = rt;
         if (first) {

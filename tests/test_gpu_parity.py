@@ -298,7 +298,9 @@ def test_tiny_and_odd_grids(pf, n):
 def test_poisson_mixed_3d_sweeps_converge(pf, n):
     """3D float32 levels use the one-pass tiled red-black sweep (ragged tiles when a
     size is not a multiple of the 32 x 8 tile): the refined solve still reaches a
-    1e-12 float64 residual of the float32 operator in few inner iterations."""
+    1e-12 float64 residual of the float32 operator in few inner iterations (a
+    faulty smoother still converges inside flexible CG, only more slowly: about
+    15 iterations here with a correct V-cycle, 25 and more with a broken one)."""
     p = I.small_case(dim=3, n=n[0], rho_in=10.0, rho_out=1.0, precision="mixed",
                      poisson_rtol=1e-12, poisson_maxit=200)
     p["n"] = n
@@ -310,7 +312,7 @@ def test_poisson_mixed_3d_sweeps_converge(pf, n):
     sim = pf.Simulation(p, phi0=phi)
     x, it, relres, st = sim.poisson_solve(rhs)
     assert st == 0 and relres <= 1e-12
-    assert it <= 40, it
+    assert it <= 20, it
     res = O.apply_poisson(beta_f32(phi, g, po), x, g) - rhs
     assert np.linalg.norm(res) <= 2e-12 * np.linalg.norm(rhs)
     sim.close()

@@ -1,0 +1,41 @@
+"""Section 3.1 spurious-current study on the batched executor (float64), at the
+two coarsest meshes of the fixed-eps panel: after the transient (t* = 250) the
+energy-based force leaves the weakest spurious currents, localized CSF the
+next, CSF the strongest, and EB converges at second order under h-refinement
+(Fig. 2a; the figure's data are not available, so its trends are what is
+checked)."""
+import math
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def study():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2205_05835_gb300 import studies as S
+
+    return S.convergence_study(panel="h", ns=(32, 64), models=("cdi",),
+                               forces=("eb", "csf", "lcsf"), tstar=250.0, nthreads=6,
+                               precision="fp64")
+
+
+def test_force_ordering_after_transient(study):
+    ca = {f: study["ca_inf"]["cdi"][f] for f in ("eb", "csf", "lcsf")}
+    for n in (32, 64):
+        assert ca["eb"][n]["ca_inf"] < ca["lcsf"][n]["ca_inf"] < ca["csf"][n]["ca_inf"], n
+        assert abs(ca["eb"][n]["t"] - 250.0 * 0.1 * 0.4) < 1e-2
+
+
+def test_eb_second_order_under_h_refinement(study):
+    o_eb = study["orders"]["cdi-eb"][0]
+    o_csf = study["orders"]["cdi-csf"][0]
+    assert 1.7 < o_eb < 2.6, o_eb
+    assert o_csf < o_eb and math.isfinite(o_csf)

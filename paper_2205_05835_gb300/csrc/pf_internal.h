@@ -154,6 +154,11 @@ bool dir3d_ok(const Dims& g);
 void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
                       const float* const* beta, int first, RedBuf rb, CGScalars* sc,
                       cudaStream_t s);
+// Restriction (mean of the children's residual) from a 3D float32 level with
+// face arrays and even sizes to the next coarser level.
+bool restrict3d_ok(const Dims& fine);
+void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const CGScalars* sc,
+                       cudaStream_t s);
 // phi != nullptr: finest level, smoother weights from rho(phi); else the
 // level's face coefficient arrays
 void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,

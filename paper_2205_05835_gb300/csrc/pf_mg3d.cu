@@ -5,13 +5,14 @@
 // and the coefficient source (rho(phi) on the finest level, the three face
 // coefficient arrays on coarser ones) is copied with a two-cell halo into
 // shared-memory rings by cp.async two planes ahead of its use, so global
-// latency overlaps the arithmetic. In the step for plane k the first six warps
-// update the first colour on plane k over the tile plus a one-cell ring (its
-// x_in neighbours are all of the other colour) and the last four warps update
-// the second colour of plane k - 2 from the new first-colour values of planes
-// k - 3 .. k - 1 and write both colours of plane k - 2: one barrier per plane.
-// The halo ring is recomputed by both neighbouring CTAs, so no CTA reads
-// another's output. Zero start (x_in = 0) skips the x_in copies.
+// latency overlaps the arithmetic. In the step for plane k the first three
+// warps update the first colour on plane k over the tile plus a one-cell ring
+// (its x_in neighbours are all of the other colour) and the last two warps
+// update the second colour of plane k - 2 from the new first-colour values of
+// planes k - 3 .. k - 1 and write both colours of plane k - 2, two cells per
+// thread: one barrier per plane. The halo ring is recomputed by both
+// neighbouring CTAs, so no CTA reads another's output. Zero start (x_in = 0)
+// skips the x_in copies.
 //
 // The smoother solves each cell's row of sum_q w_q (x_c - x_q) = f h^2 / s
 // with unscaled weights (w_q = 1 / (rho_c + rho_q), s = 2, on the finest
@@ -22,6 +23,7 @@
 // ragged (sizes need not be multiples of 32 x 8) since every index wraps.
 // Rows of the finest level are copied in 16-byte chunks when nx is a multiple
 // of 4, else (and on coarser levels) in 8-byte chunks.
+#include <cstddef>
 #include <mutex>
 
 #include "pf_device.cuh"
@@ -35,8 +37,9 @@ constexpr int HY = TY + 4;                  // rows j0-2 .. j0+TY+1 of a halo-2 
 constexpr int RXS = TX + 2, RYS = TY + 2;   // halo-1 plane (first-colour values)
 constexpr int N1 = (RXS / 2) * RYS;         // first-colour cells per plane (170)
 constexpr int N2 = (TX / 2) * TY;           // second-colour cells per plane (128)
-constexpr int W1 = 192;                     // first-colour threads: six whole warps
-constexpr int NT = W1 + N2;                 // 320 threads
+constexpr int W1 = 96;                      // first-colour threads (3 warps, 2 cells each)
+constexpr int W2 = N2 / 2;                  // second-colour threads (2 warps, 2 cells each)
+constexpr int NT = W1 + W2;                 // 160 threads
 
 // halo-2 plane geometry for copy chunks of V floats: shared-memory column a
 // holds global column i0 - OX + a
@@ -56,7 +59,6 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) { cp_async<8>(smem, gmem); }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 template <int N>
@@ -64,13 +66,6 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // ring slot of plane kp (kp >= -8)
 template <int R>
 __device__ __forceinline__ int slot(int kp) { return (int)((unsigned)(kp + 8 * R) % (unsigned)R); }
-// slot s of a ring of R moved by d in [-R, R]
-template <int R>
-__device__ __forceinline__ int rmove(int s, int d) {
-    s += d;
-    s += s < 0 ? R : 0;
-    return s >= R ? s - R : s;
-}
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -104,18 +99,34 @@ constexpr int RX_ = 3 + PD, RF_ = 4 + PD, RR_ = 5 + PD, RB_ = 4 + PD, RN_ = 4;
 template <bool FROM_PHI, int V>
 struct Smem {
     static constexpr int HX = Geo<V>::HX;
-    float x[RX_][HY][HX];
     float f[RF_][HY][HX];
     float c[FROM_PHI ? RR_ : 3 * RB_][HY][HX];
-    float n[RN_][RYS][RXS];
+    float n[RN_][RYS][RXS / 2];   // first-colour values only, (a1 >> 1) per row
+    float x[RX_][HY][HX];         // last: a zero-start launch leaves it out
 };
+
+// plane offset o (floats) of a ring of R planes of P floats, moved by d planes
+template <int R, int P>
+__device__ __forceinline__ int ring(int o, int d) {
+    o += d * P;
+    o += o < 0 ? R * P : 0;
+    return o >= R * P ? o - R * P : o;
+}
 
 template <bool FROM_PHI, int V>
 __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* smem_raw) {
     using G = Geo<V>;
     constexpr int HX = G::HX, OX = G::OX;
     constexpr int PLANE = HY * HX;   // floats per halo-2 plane
+    constexpr int RXH = RXS / 2;     // first-colour cells per halo-1 row
+    constexpr int NPL = RYS * RXH;   // floats per first-colour plane
+    constexpr int RC = FROM_PHI ? RR_ : RB_;
+    constexpr int CH = (G::NCH + NT - 1) / NT;   // copy chunks per thread
     Smem<FROM_PHI, V>& S = *reinterpret_cast<Smem<FROM_PHI, V>*>(smem_raw);
+    float* const Xs = &S.x[0][0][0];
+    float* const Fs = &S.f[0][0][0];
+    float* const Cs = &S.c[0][0][0];
+    float* const Ns = &S.n[0][0][0];
     float rz = 0.f, zq = 0.f;   // per-thread partial dots (A.dots)
 
     const Dims& g = A.g;
@@ -129,160 +140,209 @@ __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* 
     const float ro = A.ph.rho_out_f, dr = A.ph.drho_f;
     const float fs = A.fs;
 
-    // this thread's copy chunk of a halo-2 plane (fixed across planes); the
-    // second-colour warps take the first chunks
-    const int lid = tid >= W1 ? tid - W1 : tid + N2;
-    const bool has_chunk = lid < G::NCH;
-    const int pb = lid / G::CPR, pa = V * (lid - pb * G::CPR);
-    const int poff = mod(j0 - 2 + pb, g.ny) * sy + mod(i0 - OX + pa, g.nx);
-    const int so = pb * HX + pa;     // chunk offset within a plane
-    // next plane to copy: index, global plane base and ring slots
+    // this thread's copy chunks of a halo-2 plane (fixed across planes)
+    int so[CH], poff[CH];
+    bool has[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int lid = tid + c * NT;
+        has[c] = lid < G::NCH;
+        const int pb = lid / G::CPR, pa = V * (lid - pb * G::CPR);
+        poff[c] = mod(j0 - 2 + pb, g.ny) * sy + mod(i0 - OX + pa, g.nx);
+        so[c] = pb * HX + pa;
+    }
+    // next plane to copy: index, global plane base and ring plane offsets
     int kiss = z0 - 2;
     int gz = mod(kiss, g.nz) * sz;
-    int ix = slot<RX_>(kiss), iff = slot<RF_>(kiss), ic = slot<FROM_PHI ? RR_ : RB_>(kiss);
+    int ix = slot<RX_>(kiss) * PLANE, iff = slot<RF_>(kiss) * PLANE, ic = slot<RC>(kiss) * PLANE;
 
     auto issue = [&]() {
-        if (has_chunk && kiss <= z1 + 1) {
-            const int gidx = gz + poff;
-            if (!zero) cp_async<4 * V>(&S.x[0][0][0] + ix * PLANE + so, A.xin + gidx);
-            cp_async<4 * V>(&S.f[0][0][0] + iff * PLANE + so, A.f + gidx);
-            if (FROM_PHI) {
-                cp_async<4 * V>(&S.c[0][0][0] + ic * PLANE + so, A.phi + gidx);
-            } else {
-                cp_async<4 * V>(&S.c[0][0][0] + ic * PLANE + so, A.bx + gidx);
-                cp_async<4 * V>(&S.c[0][0][0] + (RB_ + ic) * PLANE + so, A.by + gidx);
-                cp_async<4 * V>(&S.c[0][0][0] + (2 * RB_ + ic) * PLANE + so, A.bz + gidx);
+        if (kiss <= z1 + 1) {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                if (!has[c]) continue;
+                const int gidx = gz + poff[c];
+                if (!zero) cp_async<4 * V>(Xs + ix + so[c], A.xin + gidx);
+                cp_async<4 * V>(Fs + iff + so[c], A.f + gidx);
+                if (FROM_PHI) {
+                    cp_async<4 * V>(Cs + ic + so[c], A.phi + gidx);
+                } else {
+                    cp_async<4 * V>(Cs + ic + so[c], A.bx + gidx);
+                    cp_async<4 * V>(Cs + RB_ * PLANE + ic + so[c], A.by + gidx);
+                    cp_async<4 * V>(Cs + 2 * RB_ * PLANE + ic + so[c], A.bz + gidx);
+                }
             }
         }
         cp_commit();
         ++kiss;
         gz += sz;
         if (gz >= g.ncell) gz -= g.ncell;
-        ix = rmove<RX_>(ix, 1);
-        iff = rmove<RF_>(iff, 1);
-        ic = rmove<FROM_PHI ? RR_ : RB_>(ic, 1);
+        ix = ring<RX_, PLANE>(ix, 1);
+        iff = ring<RF_, PLANE>(iff, 1);
+        ic = ring<RC, PLANE>(ic, 1);
     };
-    // rho(phi) in place for this thread's own chunk of the ring slot s (after
-    // its copy landed)
-    auto transform = [&](int s, bool used) {
-        if (FROM_PHI && has_chunk && used) {
-            float* c = &S.c[0][0][0] + s * PLANE + so;
+    // rho(phi) in place for this thread's own chunks of the plane at ring
+    // offset o (after their copies landed)
+    auto transform = [&](int o, bool used) {
+        if (FROM_PHI && used) {
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const float v = fminf(fmaxf(c[e], 0.f), 1.f);
-                c[e] = __fadd_rn(ro, __fmul_rn(dr, v));
+            for (int c = 0; c < CH; ++c) {
+                if (!has[c]) continue;
+                float* cp = Cs + o + so[c];
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const float v = fminf(fmaxf(cp[e], 0.f), 1.f);
+                    cp[e] = __fadd_rn(ro, __fmul_rn(dr, v));
+                }
             }
         }
     };
-    // weights -x, +x, -y, +y, -z, +z of the cell at (a, b); sc: coefficient
-    // ring slot of its plane
-    auto weights = [&](int a, int b, int sc, float (&w)[6]) {
+    // weights -x, +x, -y, +y, -z, +z of the cell at offset co of the plane at
+    // coefficient ring offset o (om, op: the planes below and above)
+    auto weights = [&](int co, int o, int om, int op, float (&w)[6]) {
         if (FROM_PHI) {
-            const float* c0p = &S.c[sc][b][a];
-            const float* cm = &S.c[rmove<RR_>(sc, -1)][b][a];
-            const float* cp = &S.c[rmove<RR_>(sc, 1)][b][a];
-            const float rc = c0p[0];
-            w[0] = rcp_approx(rc + c0p[-1]);
-            w[1] = rcp_approx(rc + c0p[1]);
-            w[2] = rcp_approx(rc + c0p[-HX]);
-            w[3] = rcp_approx(rc + c0p[HX]);
-            w[4] = rcp_approx(rc + cm[0]);
-            w[5] = rcp_approx(rc + cp[0]);
+            const float* cc = Cs + o + co;
+            const float rc = cc[0];
+            w[0] = rcp_approx(rc + cc[-1]);
+            w[1] = rcp_approx(rc + cc[1]);
+            w[2] = rcp_approx(rc + cc[-HX]);
+            w[3] = rcp_approx(rc + cc[HX]);
+            w[4] = rcp_approx(rc + Cs[om + co]);
+            w[5] = rcp_approx(rc + Cs[op + co]);
         } else {
-            const int sp = rmove<RB_>(sc, 1);
-            w[0] = S.c[sc][b][a];
-            w[1] = S.c[sc][b][a + 1];
-            w[2] = S.c[RB_ + sc][b][a];
-            w[3] = S.c[RB_ + sc][b + 1][a];
-            w[4] = S.c[2 * RB_ + sc][b][a];
-            w[5] = S.c[2 * RB_ + sp][b][a];
+            const float* cx = Cs + o + co;
+            const float* cy = cx + RB_ * PLANE;
+            w[0] = cx[0];
+            w[1] = cx[1];
+            w[2] = cy[0];
+            w[3] = cy[HX];
+            w[4] = cx[2 * RB_ * PLANE];
+            w[5] = Cs[2 * RB_ * PLANE + op + co];
         }
     };
 
-    // fixed per-thread cell coordinates: first colour (halo-1 row b1, pair m1),
-    // second colour (tile row tb, pair m2)
-    const int b1f = tid / (RXS / 2), m1 = tid - b1f * (RXS / 2);
-    const int t2 = tid - W1;
-    const int tb = t2 >> 4, m2 = t2 & 15;
+    // fixed per-thread cell offsets (two cells per thread): first colour on
+    // halo-1 cells u = tid, tid + W1 (row u / 17, pair u % 17); second colour on
+    // tile cells t, t + W2 (row t / 16, pair t % 16); each cell's colour parity
+    // flips from plane to plane
+    const bool first_grp = tid < W1;
+    int co[2], cn[2], par[2], g2[2];
+    bool act[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (first_grp) {
+            const int u = tid + h * W1;
+            act[h] = u < N1;
+            const int b1 = u / RXH, m = u - b1 * RXH;
+            co[h] = (b1 + 1) * HX + 2 * m + OX - 1;
+            cn[h] = b1 * RXH + m;
+            par[h] = (c0 + b1 + z0 - 1) & 1;
+            g2[h] = 0;
+        } else {
+            const int t = tid - W1 + h * W2;
+            const int tb = t >> 4, m = t & 15;
+            act[h] = (j0 + tb < g.ny) && (i0 + 2 * m < g.nx);
+            co[h] = (tb + 2) * HX + 2 * m + OX;
+            cn[h] = (tb + 1) * RXH + m;
+            par[h] = (c0 + 1 + tb + z0 - 3) & 1;
+            g2[h] = (z0 - 3) * sz + (j0 + tb) * sy + i0 + 2 * m;   // output of plane kb
+        }
+    }
+    // q of the second-colour cells (fused dots), loaded one plane ahead
+    const bool want_q = A.dots && !A.first && !first_grp;
+    float2 qv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (want_q && z0 < z1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (act[h]) qv[h] = __ldg(reinterpret_cast<const float2*>(A.q + g2[h] + 3 * sz));
+    }
 
     // prologue: planes z0-2, z0-1 landed; z0 .. z0+PD-1 in flight
-    constexpr int RC = FROM_PHI ? RR_ : RB_;
-    const int c_lo = slot<RC>(z0 - 2);
+    const int c_lo = slot<RC>(z0 - 2) * PLANE;
     issue();
     issue();
     cp_wait_all();
     transform(c_lo, true);
-    transform(rmove<RC>(c_lo, 1), true);
+    transform(ring<RC, PLANE>(c_lo, 1), true);
     for (int q = 0; q < PD; ++q) issue();
-    // ring slots of plane kr (x, f, coefficients, first-colour values)
-    int sx = slot<RX_>(z0 - 1), sf = slot<RF_>(z0 - 1), scr = slot<RC>(z0 - 1),
-        sn = slot<RN_>(z0 - 1);
+    // ring plane offsets of plane kr
+    int ox = slot<RX_>(z0 - 1) * PLANE, of = slot<RF_>(z0 - 1) * PLANE;
+    int oc = slot<RC>(z0 - 1) * PLANE, on = slot<RN_>(z0 - 1) * NPL;
     // step kr: first colour on plane kr (kr <= z1), second colour on kb = kr - 2
     for (int kr = z0 - 1; kr <= z1 + 1; ++kr) {
         cp_wait<PD - 1>();      // own copies of plane kr + 1 have landed
-        transform(rmove<RC>(scr, 1), kr + 1 <= z1 + 1);
+        const int ocp = ring<RC, PLANE>(oc, 1);
+        transform(ocp, kr + 1 <= z1 + 1);
         __syncthreads();        // every copy of plane kr + 1 visible; step kr - 1 done
         issue();                // plane kr + 1 + PD; overlaps with the next PD steps
-        if (tid < W1) {
-            if (tid < N1 && kr <= z1) {
-                // halo-1 (a1, b1) has the colour (a1 + b1 + k) & 1 (i0, j0, n even)
-                const int a1 = 2 * m1 + ((c0 + b1f + kr) & 1);
-                const int a = a1 - 1 + OX, b = b1f + 1;
-                float w[6];
-                weights(a, b, scr, w);
-                const float diag = w[0] + w[1] + w[2] + w[3] + w[4] + w[5];
-                float num = S.f[sf][b][a] * fs;
-                if (!zero) {
-                    const float* xc = &S.x[sx][b][a];
-                    num += w[0] * xc[-1] + w[1] * xc[1] + w[2] * xc[-HX] + w[3] * xc[HX] +
-                           w[4] * S.x[rmove<RX_>(sx, -1)][b][a] +
-                           w[5] * S.x[rmove<RX_>(sx, 1)][b][a];
+        if (first_grp) {
+            if (kr <= z1) {
+                const int ocm = ring<RC, PLANE>(oc, -1);
+                const int oxm = ring<RX_, PLANE>(ox, -1), oxp = ring<RX_, PLANE>(ox, 1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!act[h]) continue;
+                    const int c = co[h] + par[h];
+                    float w[6];
+                    weights(c, oc, ocm, ocp, w);
+                    const float diag = w[0] + w[1] + w[2] + w[3] + w[4] + w[5];
+                    float num = Fs[of + c] * fs;
+                    if (!zero) {
+                        const float* xc = Xs + ox + c;
+                        num += w[0] * xc[-1] + w[1] * xc[1] + w[2] * xc[-HX] + w[3] * xc[HX] +
+                               w[4] * Xs[oxm + c] + w[5] * Xs[oxp + c];
+                    }
+                    Ns[on + cn[h]] = num * rcp_approx(diag);
                 }
-                S.n[sn][b1f][a1] = num * rcp_approx(diag);
             }
         } else {
             const int kb = kr - 2;
             if (kb >= z0 && kb < z1) {
-                const int snb = rmove<RN_>(sn, -2), snm = rmove<RN_>(sn, -3),
-                          snp = rmove<RN_>(sn, -1);
-                const int sfb = rmove<RF_>(sf, -2);
-                // interior (ta, tb) has the colour (ta + tb + k) & 1; second colour 1 - c0
-                const int s2 = (c0 + 1 + tb + kb) & 1;
-                const int ta = 2 * m2 + s2;
-                const int a = ta + OX, b = tb + 2;
-                const int a1 = ta + 1, b1 = tb + 1;
-                float w[6];
-                weights(a, b, rmove<RC>(scr, -2), w);
-                const float diag = w[0] + w[1] + w[2] + w[3] + w[4] + w[5];
-                const float* nc = &S.n[snb][b1][a1];
-                const float num = S.f[sfb][b][a] * fs + w[0] * nc[-1] + w[1] * nc[1] +
-                                  w[2] * nc[-RXS] + w[3] * nc[RXS] +
-                                  w[4] * S.n[snm][b1][a1] + w[5] * S.n[snp][b1][a1];
-                const float v2 = num * rcp_approx(diag);
-                // the pair (2 m2, 2 m2 + 1) of this row holds one cell of each colour
-                const int ea = 2 * m2;
-                const float v_even = s2 == 0 ? v2 : S.n[snb][b1][ea + 1];
-                const float v_odd = s2 == 1 ? v2 : S.n[snb][b1][ea + 2];
-                const int gi = i0 + ea, gj = j0 + tb;
-                if (gj < g.ny && gi < g.nx) {
-                    const int kk = kb < 0 ? kb + g.nz : (kb >= g.nz ? kb - g.nz : kb);
-                    float* out = A.xout + kk * sz + gj * sy + gi;
-                    *reinterpret_cast<float2*>(out) = make_float2(v_even, v_odd);
-                    if (A.dots) {
-                        rz += S.f[sfb][b][ea + OX] * v_even + S.f[sfb][b][ea + OX + 1] * v_odd;
-                        if (!A.first) {
-                            const float2 qq = __ldg(reinterpret_cast<const float2*>(
-                                A.q + (kk * sz + gj * sy + gi)));
-                            zq += v_even * qq.x + v_odd * qq.y;
+                const int onb = ring<RN_, NPL>(on, -2), onm = ring<RN_, NPL>(on, -3),
+                          onp = ring<RN_, NPL>(on, -1);
+                const int ofb = ring<RF_, PLANE>(of, -2);
+                const int ocb = ring<RC, PLANE>(oc, -2), ocbm = ring<RC, PLANE>(oc, -3),
+                          ocbp = ring<RC, PLANE>(oc, -1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int s2 = par[h];
+                    const int c = co[h] + s2;
+                    float w[6];
+                    weights(c, ocb, ocbm, ocbp, w);
+                    const float diag = w[0] + w[1] + w[2] + w[3] + w[4] + w[5];
+                    // first-colour neighbours: x at (a1 -+ 1) >> 1, the rest at a1 >> 1
+                    const float* nc = Ns + onb + cn[h];
+                    const float num = Fs[ofb + c] * fs + w[0] * nc[0] + w[1] * nc[1] +
+                                      w[2] * nc[s2 - RXH] + w[3] * nc[s2 + RXH] +
+                                      w[4] * Ns[onm + cn[h] + s2] + w[5] * Ns[onp + cn[h] + s2];
+                    const float v2 = num * rcp_approx(diag);
+                    // the pair (2 m, 2 m + 1) of this row holds one cell of each colour
+                    const float other = nc[1 - s2];
+                    const float v_even = s2 == 0 ? v2 : other;
+                    const float v_odd = s2 == 1 ? v2 : other;
+                    if (act[h]) {
+                        *reinterpret_cast<float2*>(A.xout + g2[h]) = make_float2(v_even, v_odd);
+                        if (A.dots) {
+                            rz += Fs[ofb + co[h]] * v_even + Fs[ofb + co[h] + 1] * v_odd;
+                            if (want_q) {
+                                zq += v_even * qv[h].x + v_odd * qv[h].y;
+                                if (kb + 1 < z1)
+                                    qv[h] = __ldg(
+                                        reinterpret_cast<const float2*>(A.q + g2[h] + sz));
+                            }
                         }
                     }
                 }
             }
         }
-        sx = rmove<RX_>(sx, 1);
-        sf = rmove<RF_>(sf, 1);
-        scr = rmove<RC>(scr, 1);
-        sn = rmove<RN_>(sn, 1);
+        ox = ring<RX_, PLANE>(ox, 1);
+        of = ring<RF_, PLANE>(of, 1);
+        oc = ocp;
+        on = ring<RN_, NPL>(on, 1);
+        par[0] ^= 1;
+        par[1] ^= 1;
+        g2[0] += sz;
+        g2[1] += sz;
     }
     cp_wait_all();
     if (A.dots) {
@@ -301,7 +361,7 @@ __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* 
 // finest level (coefficients from phi) and coarser levels (face arrays), in
 // 16-byte (V = 4) or 8-byte (V = 2) copy chunks
 template <bool FROM_PHI, int V>
-__global__ void __launch_bounds__(NT, FROM_PHI ? 5 : 4) k_sweep3d(SweepArgs A, const CGScalars* sc) {
+__global__ void __launch_bounds__(NT, FROM_PHI ? 6 : 4) k_sweep3d(SweepArgs A, const CGScalars* sc) {
     if (sc && (sc->done || sc->idone)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     sweep3d_body<FROM_PHI, V>(A, smem_raw);
@@ -309,6 +369,9 @@ __global__ void __launch_bounds__(NT, FROM_PHI ? 5 : 4) k_sweep3d(SweepArgs A, c
 
 template <bool FROM_PHI, int V>
 void launch_sweep3d_t(const SweepArgs& a, dim3 grid, const CGScalars* sc, cudaStream_t s) {
+    // a zero-start sweep copies no x_in: its launch leaves out the x ring
+    using SM = Smem<FROM_PHI, V>;
+    const size_t bytes = a.xin == nullptr ? offsetof(SM, x) : sizeof(SM);
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
         // dynamic shared memory beyond 48 KB, and a shared-memory carveout that
@@ -318,7 +381,7 @@ void launch_sweep3d_t(const SweepArgs& a, dim3 grid, const CGScalars* sc, cudaSt
         cudaFuncSetAttribute(k_sweep3d<FROM_PHI, V>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     });
-    k_sweep3d<FROM_PHI, V><<<grid, NT, sizeof(Smem<FROM_PHI, V>), s>>>(a, sc);
+    k_sweep3d<FROM_PHI, V><<<grid, NT, bytes, s>>>(a, sc);
 }
 
 }  // namespace
@@ -435,33 +498,73 @@ __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
         const int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
         const int col = j * sy + i;
         const int ox_m = im - i, ox_p = ip - i, oy_m = (jm - j) * sy, oy_p = (jp - j) * sy;
+        const float* __restrict__ zp = A.z;
+        const float* __restrict__ po = A.p_old;
+        const float* __restrict__ bxp = A.bx;
+        const float* __restrict__ byp = A.by;
+        const float* __restrict__ bzp = A.bz;
+        float* __restrict__ pnew = A.p_new;
+        float* __restrict__ qo = A.q;
+        const bool first = A.first;
         auto pn = [&](int idx) {
-            const float zv = __ldg(A.z + idx);
-            return A.first ? zv : zv + bcg * __ldg(A.p_old + idx);
+            const float zv = __ldg(zp + idx);
+            return first ? zv : zv + bcg * __ldg(po + idx);
         };
         const int km1 = z0 == 0 ? g.nz - 1 : z0 - 1;
         float p_m = pn(km1 * sz + col);
         float p_c = pn(z0 * sz + col);
-        float bz_c = __ldg(A.bz + z0 * sz + col);
-#pragma unroll 2
-        for (int k = z0; k < z1; ++k) {
-            const int kp = k + 1 == g.nz ? 0 : k + 1;
+        float bz_c = __ldg(bzp + z0 * sz + col);
+        // the loads of plane k: in-plane neighbours of p_new (as z, p_old), the
+        // x / y face coefficients, and the centre of plane k + 1 with its z face
+        struct Ld {
+            float z[4], p[4], bx0, bx1, by0, by1, zn, pnx, bzn;
+        };
+        auto load = [&](int k, Ld& L) {
             const int idx = k * sz + col;
-            const int idxp = kp * sz + col;
-            const float p_p = pn(idxp);
-            const float bz_p = __ldg(A.bz + idxp);
-            const float ax = __ldg(A.bx + idx) * (p_c - pn(idx + ox_m)) +
-                             __ldg(A.bx + idx + ox_p) * (p_c - pn(idx + ox_p)) +
-                             __ldg(A.by + idx) * (p_c - pn(idx + oy_m)) +
-                             __ldg(A.by + idx + oy_p) * (p_c - pn(idx + oy_p)) +
-                             bz_c * (p_c - p_m) + bz_p * (p_c - p_p);
+            const int idxp = (k + 1 == g.nz ? 0 : k + 1) * sz + col;
+            const int o[4] = {idx + ox_m, idx + ox_p, idx + oy_m, idx + oy_p};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                L.z[q] = __ldg(zp + o[q]);
+                L.p[q] = first ? 0.f : __ldg(po + o[q]);
+            }
+            L.bx0 = __ldg(bxp + idx);
+            L.bx1 = __ldg(bxp + idx + ox_p);
+            L.by0 = __ldg(byp + idx);
+            L.by1 = __ldg(byp + idx + oy_p);
+            L.zn = __ldg(zp + idxp);
+            L.pnx = first ? 0.f : __ldg(po + idxp);
+            L.bzn = __ldg(bzp + idxp);
+        };
+        auto apply = [&](int k, const Ld& L) {
+            const int idx = k * sz + col;
+            const float p_p = L.zn + bcg * L.pnx;
+            float nb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nb[q] = L.z[q] + bcg * L.p[q];
+            const float ax = L.bx0 * (p_c - nb[0]) + L.bx1 * (p_c - nb[1]) + L.by0 * (p_c - nb[2]) +
+                             L.by1 * (p_c - nb[3]) + bz_c * (p_c - p_m) + L.bzn * (p_c - p_p);
             const float qv = ax * A.ih2;
-            A.p_new[idx] = p_c;
-            A.q[idx] = qv;
+            pnew[idx] = p_c;
+            qo[idx] = qv;
             pq += p_c * qv;
             p_m = p_c;
             p_c = p_p;
-            bz_c = bz_p;
+            bz_c = L.bzn;
+        };
+        // two planes per round: all loads of both before the arithmetic
+        int k = z0;
+        for (; k + 1 < z1; k += 2) {
+            Ld a, b;
+            load(k, a);
+            load(k + 1, b);
+            apply(k, a);
+            apply(k + 1, b);
+        }
+        if (k < z1) {
+            Ld a;
+            load(k, a);
+            apply(k, a);
         }
     }
     double v[1] = {double(pq)}, tot[1];
@@ -496,6 +599,126 @@ void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* 
     a.zc = zc;
     dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
     k_dir3d_reg<<<grid, 256, 0, s>>>(a);
+}
+
+}  // namespace pf
+
+// ---------------------------------------------------------------------------
+// Restriction on 3D float32 levels with face arrays: f_C(I) = mean over the 8
+// children of the fine residual f - A x. One thread per coarse column (I, J)
+// marching in z; the 2 x 2 fine block of the planes k - 1, k, k + 1 and the
+// z-face coefficients are carried in registers, the in-plane neighbours and
+// coefficients come through L1 as pairs.
+// ---------------------------------------------------------------------------
+namespace pf {
+namespace {
+
+struct RestrictArgs {
+    Dims fg, cg;
+    const float* x;
+    const float* f;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    float* cf;
+    int zc;   // coarse planes per CTA
+};
+
+__global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CGScalars* sc) {
+    if (sc->done || sc->idone) return;
+    const int I = blockIdx.x * 32 + threadIdx.x % 32;
+    const int J = blockIdx.y * 8 + threadIdx.x / 32;
+    const Dims& g = A.fg;
+    if (I >= A.cg.nx || J >= A.cg.ny) return;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, sz = nx * ny;
+    const int i = 2 * I, j = 2 * J;
+    const int im = i == 0 ? nx - 1 : i - 1, ip2 = i + 2 == nx ? 0 : i + 2;
+    const int r0 = j * nx, r1 = r0 + nx;
+    const int rs = (j == 0 ? ny - 1 : j - 1) * nx, rn = (j + 2 == ny ? 0 : j + 2) * nx;
+    const float ih2 = g.ih2f;
+    const float* __restrict__ x = A.x;
+    const float* __restrict__ f = A.f;
+    const float* __restrict__ bx = A.bx;
+    const float* __restrict__ by = A.by;
+    const float* __restrict__ bz = A.bz;
+    auto pair = [](const float* a, int o) { return __ldg(reinterpret_cast<const float2*>(a + o)); };
+    float* __restrict__ cf = A.cf;
+    const int K0 = blockIdx.z * A.zc;
+    const int K1 = min(K0 + A.zc, A.cg.nz);
+    // 2 x 2 blocks (rows j, j + 1 as pairs) of planes k - 1 (m), k (c), k + 1 (p)
+    int k = 2 * K0;
+    int kb = k * sz;
+    const int kbm = (k == 0 ? nz - 1 : k - 1) * sz;
+    float2 m0 = pair(x, kbm + r0 + i), m1 = pair(x, kbm + r1 + i);
+    float2 c0 = pair(x, kb + r0 + i), c1 = pair(x, kb + r1 + i);
+    float2 zc0 = pair(bz, kb + r0 + i), zc1 = pair(bz, kb + r1 + i);
+    for (int K = K0; K < K1; ++K) {
+        float s = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h, ++k) {
+            const int kp = k + 1 == nz ? 0 : k + 1;
+            const int kpb = kp * sz;
+            const float2 p0 = pair(x, kpb + r0 + i), p1 = pair(x, kpb + r1 + i);
+            const float2 zp0 = pair(bz, kpb + r0 + i), zp1 = pair(bz, kpb + r1 + i);
+            // in-plane neighbours and coefficients of plane k
+            const float xl0 = __ldg(x + kb + r0 + im), xl1 = __ldg(x + kb + r1 + im);
+            const float xr0 = __ldg(x + kb + r0 + ip2), xr1 = __ldg(x + kb + r1 + ip2);
+            const float2 xs = pair(x, kb + rs + i), xn = pair(x, kb + rn + i);
+            const float2 bx0 = pair(bx, kb + r0 + i), bx1 = pair(bx, kb + r1 + i);
+            const float bxr0 = __ldg(bx + kb + r0 + ip2), bxr1 = __ldg(bx + kb + r1 + ip2);
+            const float2 by0 = pair(by, kb + r0 + i), by1 = pair(by, kb + r1 + i),
+                         by2 = pair(by, kb + rn + i);
+            const float2 f0 = pair(f, kb + r0 + i), f1 = pair(f, kb + r1 + i);
+            // children in the order (x fastest, then y) of the plane
+            const float a00 = bx0.x * (c0.x - xl0) + bx0.y * (c0.x - c0.y) +
+                              by0.x * (c0.x - xs.x) + by1.x * (c0.x - c1.x) +
+                              zc0.x * (c0.x - m0.x) + zp0.x * (c0.x - p0.x);
+            const float a10 = bx0.y * (c0.y - c0.x) + bxr0 * (c0.y - xr0) +
+                              by0.y * (c0.y - xs.y) + by1.y * (c0.y - c1.y) +
+                              zc0.y * (c0.y - m0.y) + zp0.y * (c0.y - p0.y);
+            const float a01 = bx1.x * (c1.x - xl1) + bx1.y * (c1.x - c1.y) +
+                              by1.x * (c1.x - c0.x) + by2.x * (c1.x - xn.x) +
+                              zc1.x * (c1.x - m1.x) + zp1.x * (c1.x - p1.x);
+            const float a11 = bx1.y * (c1.y - c1.x) + bxr1 * (c1.y - xr1) +
+                              by1.y * (c1.y - c0.y) + by2.y * (c1.y - xn.y) +
+                              zc1.y * (c1.y - m1.y) + zp1.y * (c1.y - p1.y);
+            s += ((f0.x - ih2 * a00) + (f0.y - ih2 * a10)) + ((f1.x - ih2 * a01) + (f1.y - ih2 * a11));
+            m0 = c0;
+            m1 = c1;
+            c0 = p0;
+            c1 = p1;
+            zc0 = zp0;
+            zc1 = zp1;
+            kb = kpb;
+        }
+        cf[(K * A.cg.ny + J) * A.cg.nx + I] = 0.125f * s;
+    }
+}
+
+}  // namespace
+
+bool restrict3d_ok(const Dims& fine) {
+    return fine.nz > 1 && fine.nx % 2 == 0 && fine.ny % 2 == 0 && fine.nz % 2 == 0 &&
+           fine.nx >= 4 && fine.ny >= 4 && fine.nz >= 4;
+}
+
+void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const CGScalars* sc,
+                       cudaStream_t s) {
+    RestrictArgs a;
+    a.fg = F.g;
+    a.cg = C.g;
+    a.x = F.x;
+    a.f = F.f;
+    a.bx = F.beta[0];
+    a.by = F.beta[1];
+    a.bz = F.beta[2];
+    a.cf = C.f;
+    const int cols = ((C.g.nx + 31) / 32) * ((C.g.ny + 7) / 8);
+    int zc = 32;
+    while (zc > 1 && (long long)cols * ((C.g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
+    a.zc = zc;
+    dim3 grid((C.g.nx + 31) / 32, (C.g.ny + 7) / 8, (C.g.nz + zc - 1) / zc);
+    k_restrict3d_reg<<<grid, 256, 0, s>>>(a, sc);
 }
 
 }  // namespace pf

@@ -440,8 +440,17 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
         }
         L.x = pre_buf[l];
         pr->begin(KC_RESTRICT);
-        k_restrict<T, DIM><<<row_grid(H.lev[l + 1].g, kThreads, 1 << 30), kThreads, 0, s>>>(
-            L, H.lev[l + 1], phi, ph, sc);
+        bool done_r = false;
+        if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+            if (L.beta[0] != nullptr && restrict3d_ok(L.g)) {
+                launch_restrict3d(reinterpret_cast<const MGLevel<float>&>(L),
+                                  reinterpret_cast<const MGLevel<float>&>(H.lev[l + 1]), sc, s);
+                done_r = true;
+            }
+        }
+        if (!done_r)
+            k_restrict<T, DIM><<<row_grid(H.lev[l + 1].g, kThreads, 1 << 30), kThreads, 0, s>>>(
+                L, H.lev[l + 1], phi, ph, sc);
         pr->end();
     }
     pr->begin(KC_COARSE);
@@ -603,6 +612,25 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_ir_addcorr(Dims g, SolveIO<T, DIM> io, const CGScalars* sc) {
     if (sc->done) return;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if ((g.ncell & 3) == 0) {
+            const int n4 = g.ncell >> 2;
+            const float4* __restrict__ e4 = reinterpret_cast<const float4*>(io.e);
+            double2* __restrict__ x2 = reinterpret_cast<double2*>(io.x);
+            const int stride = gridDim.x * blockDim.x;
+            for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+                const float4 ev = e4[t];
+                double2 a = x2[2 * t], b = x2[2 * t + 1];
+                a.x += double(ev.x);
+                a.y += double(ev.y);
+                b.x += double(ev.z);
+                b.y += double(ev.w);
+                x2[2 * t] = a;
+                x2[2 * t + 1] = b;
+            }
+            return;
+        }
+    }
     for_cells(g, [&](int, int, int, int idx) { io.x[idx] += double(io.e[idx]); });
 }
 
@@ -690,13 +718,46 @@ k_in_update(Dims g, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGScalars
     const T alpha = T(sc->alpha);
     const T* __restrict__ pn = cur ? io.p[0] : io.p[1];
     T rr = T(0);   // per-thread partial in T, float64 across threads
-    for_cells(g, [&](int, int, int, int idx) {
-        const T pv = pn[idx];
-        io.e[idx] = first ? alpha * pv : io.e[idx] + alpha * pv;
-        const T rv = io.r[idx] - alpha * io.q[idx];
-        io.r[idx] = rv;
-        rr += rv * rv;
-    });
+    bool done = false;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // float32 vectors in 16-byte pieces (sub-buffers are 256-byte aligned):
+        // four times the bytes in flight per load
+        if ((g.ncell & 3) == 0) {
+            const int n4 = g.ncell >> 2;
+            const float4* __restrict__ p4 = reinterpret_cast<const float4*>(pn);
+            const float4* __restrict__ q4 = reinterpret_cast<const float4*>(io.q);
+            float4* __restrict__ e4 = reinterpret_cast<float4*>(io.e);
+            float4* __restrict__ r4 = reinterpret_cast<float4*>(io.r);
+            const int stride = gridDim.x * blockDim.x;
+#pragma unroll 2
+            for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+                const float4 pv = p4[t], qv = q4[t];
+                float4 rv = r4[t];
+                float4 ev = first ? make_float4(0.f, 0.f, 0.f, 0.f) : e4[t];
+                ev.x += alpha * pv.x;
+                ev.y += alpha * pv.y;
+                ev.z += alpha * pv.z;
+                ev.w += alpha * pv.w;
+                rv.x -= alpha * qv.x;
+                rv.y -= alpha * qv.y;
+                rv.z -= alpha * qv.z;
+                rv.w -= alpha * qv.w;
+                e4[t] = ev;
+                r4[t] = rv;
+                rr += (rv.x * rv.x + rv.y * rv.y) + (rv.z * rv.z + rv.w * rv.w);
+            }
+            done = true;
+        }
+    }
+    if (!done) {
+        for_cells(g, [&](int, int, int, int idx) {
+            const T pv = pn[idx];
+            io.e[idx] = first ? alpha * pv : io.e[idx] + alpha * pv;
+            const T rv = io.r[idx] - alpha * io.q[idx];
+            io.r[idx] = rv;
+            rr += rv * rv;
+        });
+    }
     double v[1] = {double(rr)}, tot[1];
     const int mode[1] = {0};
     if (grid_reduce<1>(v, mode, rb, tot) && threadIdx.x == 0) {

@@ -137,6 +137,14 @@ class ClockSampler:
 # Algorithmic bytes per cell and launch of each kernel class on the mixed 3D
 # path (float32 fields and face coefficients, float64 pressure and divergence;
 # derivation in the design doc).
+# DRAM bytes per cell per launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the 256^3 case of the same kernel, mean of the
+# pre- and post-smoothing launches (profiles/k_sweep3d_finest_osc256_mixed.md:
+# 10.9 and 20.2 B/cell); scaled to a launch by the cell count. Valid for the
+# kernel as profiled; None for every other class.
+NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 15.55}
+
+
 def algo_bytes_per_cell(cls, dim, w):
     d = dim
     table = {
@@ -339,7 +347,10 @@ def run_ours(args, rank, world, local_rank):
         achieved = bpc * ncell / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "algo_bytes_per_launch": bpc * ncell,
+                "traffic": (NCU_TRAFFIC_PER_CELL[dom] * ncell
+                            if dom in NCU_TRAFFIC_PER_CELL and p["dim"] == 3
+                            and p.get("precision") == "mixed" else None),
+                "algo_bytes_per_launch": bpc * ncell,
                 "avg_launch_us": avg_s * 1e6,
                 "share_of_step": dom_ms / ms if ms > 0 else None}
 

@@ -82,6 +82,33 @@ def measured_hbm():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def bind_to_gpu_host_cpus(index):
+    """Restrict this process to the host CPUs attached to GPU `index` (its PCI
+    device's local_cpulist), so that pinned host buffers are allocated in the
+    GPU's local memory node; returns the CPU list or None when unknown."""
+    import torch
+
+    try:
+        pr = torch.cuda.get_device_properties(index)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return text
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -289,6 +316,7 @@ def run_ours(args, rank, world, local_rank):
     import paper_2205_05835_gb300 as pf
 
     torch.cuda.set_device(local_rank)
+    host_cpus = bind_to_gpu_host_cpus(local_rank)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -297,6 +325,8 @@ def run_ours(args, rank, world, local_rank):
     p, desc = workload(args.workload, args.n)
     if args.inner_tol is not None:
         p["inner_tol"] = args.inner_tol
+    if args.mg_sweeps is not None:
+        p["mg_pre"] = p["mg_post"] = args.mg_sweeps
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = pf.Simulation(p, stream=stream)
@@ -363,15 +393,27 @@ def run_ours(args, rank, world, local_rank):
         pf.pf_get_state(sim.ctx, h_in.data_ptr())
         e2e_steps = max(1, min(args.steps, 5))
         barrier()
+        t_h2d = t_step = t_d2h = 0.0
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            pf.pf_set_state(sim.ctx, h_in.data_ptr())
+            ta = time.perf_counter()
+            pf.pf_set_state(sim.ctx, h_in.data_ptr())      # synchronises
+            tb = time.perf_counter()
             sim.step(1)
-            pf.pf_get_state(sim.ctx, h_out.data_ptr())
+            pf.pf_sync(sim.ctx)
+            tc = time.perf_counter()
+            pf.pf_get_state(sim.ctx, h_out.data_ptr())     # synchronises
+            td = time.perf_counter()
+            t_h2d += tb - ta
+            t_step += tc - tb
+            t_d2h += td - tc
         barrier()
         et = time.perf_counter() - t0
         e2e = {"value": ncell * world * e2e_steps / et / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": e2e_steps}
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": e2e_steps,
+               "host_cpus": host_cpus,
+               "ms_per_step": {"h2d": 1e3 * t_h2d / e2e_steps, "step": 1e3 * t_step / e2e_steps,
+                               "d2h": 1e3 * t_d2h / e2e_steps}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -413,6 +455,8 @@ def main():
     ap.add_argument("--threads", type=int, default=16, help="host threads (batch workload)")
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="relative reduction of each float32 inner solve (mixed path)")
+    ap.add_argument("--mg-sweeps", type=int, default=None,
+                    help="pre- and post-smoothing sweeps per V-cycle (tuning; default 1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -89,7 +89,7 @@ typedef struct {
     int pert_mode;        /* surface perturbation mode n (0: none) */
     double pert_amp;      /* relative amplitude a: R(theta) = R (1 + a cos n theta) [2D],
                              R (1 + a P_n(cos theta)) [3D] */
-    int mg_pre, mg_post;  /* red-black Gauss-Seidel sweeps before/after coarse correction (0: 1) */
+    int mg_pre, mg_post;  /* red-black Gauss-Seidel sweeps before/after coarse correction, 0..16 (0: 1) */
     double bound_tol;     /* > 0: flag PF_ERR_UNBOUNDED when phi leaves [-tol, 1 + tol] */
     double inner_tol;     /* mixed precision: relative residual reduction of each float32
                              inner solve between float64 refinements (0: 1e-6) */

@@ -131,6 +131,10 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "viscosities, sigma and delta_n must be non-negative";
         return PF_ERR_INVALID;
     }
+    if (p->mg_pre < 0 || p->mg_pre > 16 || p->mg_post < 0 || p->mg_post > 16) {
+        why = "mg_pre and mg_post must be in [0, 16] (0: one sweep)";
+        return PF_ERR_INVALID;
+    }
     if (p->inner_tol < 0 || p->inner_tol >= 1) {
         why = "inner_tol must be in [0, 1)";
         return PF_ERR_INVALID;

@@ -159,6 +159,14 @@ void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* 
 bool restrict3d_ok(const Dims& fine);
 void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const CGScalars* sc,
                        cudaStream_t s);
+// Column-marching per-stage kernels for 3D float32 grids (pf_stage3d.cu).
+void launch_cell_pass_mu3d(const Dims& g, const Phys& ph, const float* phi, float* n0, float* n1,
+                           float* n2, float* mu, cudaStream_t s);
+bool divergence3d_ok(const Dims& g);
+void launch_divergence3d(const Dims& g, const float* const* u, double inv_tau, double* b,
+                         RedBuf rb, CGScalars* sc, cudaStream_t s);
+void launch_correct3d(const Dims& g, const float* const* beta32, const float* const* ustar,
+                      const double* p, double tau, float* const* uout, cudaStream_t s);
 // phi != nullptr: finest level, smoother weights from rho(phi); else the
 // level's face coefficient arrays
 void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,

@@ -432,7 +432,13 @@ void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, c
         a.rb = RedBuf{nullptr, nullptr};
         a.scw = nullptr;
     }
-    const int zc = tiled_zc(L.g);
+    // 64-plane chunks where that still gives 8 CTAs per SM (the z halo and
+    // the pipeline start are paid once per chunk), else the shared choice
+    int zc = tiled_zc(L.g);
+    {
+        const long long cols = (long long)((L.g.nx + TX - 1) / TX) * ((L.g.ny + TY - 1) / TY);
+        if (zc == 32 && cols * ((L.g.nz + 63) / 64) >= 8 * 152) zc = 64;
+    }
     a.zc = zc;
     dim3 grid((L.g.nx + TX - 1) / TX, (L.g.ny + TY - 1) / TY, (L.g.nz + zc - 1) / zc);
     if (dots && 2LL * grid.x * grid.y * grid.z > (long long)kRedPart) {

@@ -417,19 +417,20 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
         MGLevel<T> L = H.lev[l];
         if (tiled_level<T, DIM>(L)) {
             if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
-                T* a = L.x;
-                T* b = L.x2;
+                // the zero-start sweep writes x; each further sweep reads the
+                // current buffer and writes the other
+                T* cur = L.x;
+                T* oth = L.x2;
                 for (int p = 0; p < H.pre; ++p) {
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
                     launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
                                    l == 0 ? reinterpret_cast<const float*>(phi) : nullptr, ph,
-                                   p == 0 ? nullptr : reinterpret_cast<const float*>(b),
-                                   reinterpret_cast<float*>(p == 0 ? a : (p % 2 ? b : a)), nullptr,
-                                   0, sc, s);
+                                   p == 0 ? nullptr : reinterpret_cast<const float*>(cur),
+                                   reinterpret_cast<float*>(p == 0 ? cur : oth), nullptr, 0, sc, s);
                     pr->end();
-                    if (p > 0) { T* t = a; a = b; b = t; }
+                    if (p > 0) { T* t = cur; cur = oth; oth = t; }
                 }
-                pre_buf[l] = a;
+                pre_buf[l] = cur;
             }
         } else {
             for (int p = 0; p < H.pre; ++p) {

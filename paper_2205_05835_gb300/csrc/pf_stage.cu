@@ -177,6 +177,12 @@ void launch_cell_pass(const Dims& g, const Phys& ph, const T* phi, T* nrm0, T* n
     } else {
         kap = aux;
     }
+    if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        if (mu != nullptr && kap == nullptr) {
+            launch_cell_pass_mu3d(g, ph, phi, nrm0, nrm1, nrm2, mu, s);
+            return;
+        }
+    }
     k_cell_pass<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(g, ph, phi, nrm0, nrm1,
                                                                               nrm2, mu, kap);
 }
@@ -343,9 +349,183 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
     });
 }
 
+// The same stage on 3D float32 grids, one thread per (i, j) column of a
+// 32 x 8 tile marching along z: the periodic neighbour offsets of the column
+// are formed once (x, y) or once per plane (z), so every neighbour is one
+// address add; the arithmetic is that of k_stage, term by term.
+__global__ void __launch_bounds__(256)
+k_stage3d(Dims g, Phys ph, StageIO<float> io, int stage, int scheme, float wdt, float cdt,
+          int write_rhs, int zc) {
+    const int i = blockIdx.x * 32 + threadIdx.x % 32;
+    const int j = blockIdx.y * 8 + threadIdx.x / 32;
+    if (i >= g.nx || j >= g.ny) return;
+    const PC<float> pcs = pc_of(ph, float());
+    const float gam = float(*io.gamma);
+    const float inv_h = g.ihf, inv2h = g.i2hf, inv_h2 = g.ih2f;
+    const float eps = pcs.eps, sigma = pcs.sigma;
+    const int sz = g.nx * g.ny;
+    const int col = j * g.nx + i;
+    int om[3], op[3];   // offsets of the -1 / +1 neighbour along x, y, z
+    om[0] = (i == 0 ? g.nx - 1 : i - 1) - i;
+    op[0] = (i == g.nx - 1 ? 0 : i + 1) - i;
+    om[1] = ((j == 0 ? g.ny - 1 : j - 1) - j) * g.nx;
+    op[1] = ((j == g.ny - 1 ? 0 : j + 1) - j) * g.nx;
+    const float* __restrict__ phi = io.phi_s;
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+    for (int k = z0; k < z1; ++k) {
+        om[2] = ((k == 0 ? g.nz - 1 : k - 1) - k) * sz;
+        op[2] = ((k == g.nz - 1 ? 0 : k + 1) - k) * sz;
+        const int idx = k * sz + col;
+        auto at = [&](const float* a, int o) { return __ldg(a + idx + o); };
+        const float pc = at(phi, 0);
+
+        // ---------------- phase field (Eq. 1, Table 1) ----------------
+        float kphi = 0.f;
+        if (ph.model == 0) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float* __restrict__ nd = io.nrm[d];
+                const float* __restrict__ ud = io.u_s[d];
+                const float pm = at(phi, om[d]);
+                const float pf = 0.5f * (pc + pm);
+                const float nf = 0.5f * (at(nd, 0) + at(nd, om[d]));
+                const float Flo = at(ud, 0) * pf - gam * (eps * ((pc - pm) * inv_h) - pf * (1.f - pf) * nf);
+                const float pp = at(phi, op[d]);
+                const float pf2 = 0.5f * (pp + pc);
+                const float nf2 = 0.5f * (at(nd, op[d]) + at(nd, 0));
+                const float Fhi = at(ud, op[d]) * pf2 - gam * (eps * ((pp - pc) * inv_h) - pf2 * (1.f - pf2) * nf2);
+                kphi = kphi - (Fhi - Flo) * inv_h;
+            }
+        } else {
+            float lap = 0.f, g2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float* __restrict__ ud = io.u_s[d];
+                const float pm = at(phi, om[d]);
+                const float pp = at(phi, op[d]);
+                const float Flo = at(ud, 0) * (0.5f * (pc + pm));
+                const float Fhi = at(ud, op[d]) * (0.5f * (pp + pc));
+                kphi = kphi - (Fhi - Flo) * inv_h;
+                lap = lap + (pp - 2.f * pc + pm) * inv_h2;
+                const float gd = (pp - pm) * inv2h;
+                g2 = g2 + gd * gd;
+            }
+            const float* kap = (ph.force == 0) ? io.aux + g.ncell : io.aux;
+            const float kc = at(kap, 0);
+            const float third = (ph.model == 1) ? eps * sqrtf(g2) * kc : pc * (1.f - pc) * kc;
+            const float dp = dwell32(pc, 1.f, 0.f);
+            kphi = kphi + gam * (eps * lap - divq(dp, eps) + third);
+        }
+
+        // ---------------- momentum at the low faces ----------------
+        float ku[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float* __restrict__ ud = io.u_s[d];
+            const int im = om[d];
+            const float pm = at(phi, im);
+            const float udc = at(ud, 0);
+            // advection -(u.grad) u_d, central, transverse components from 4 faces
+            float adv = 0.f;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                float vel;
+                if (e == d) {
+                    vel = udc;
+                } else {
+                    const float* __restrict__ ue = io.u_s[e];
+                    vel = 0.25f * (at(ue, 0) + at(ue, op[e]) + at(ue, im) + at(ue, im + op[e]));
+                }
+                adv = adv + vel * ((at(ud, op[e]) - at(ud, om[e])) * inv2h);
+            }
+            // viscous stress divergence
+            float visc = 0.f;
+            const float etac = eta_of(pc, pcs), etam = eta_of(pm, pcs);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                if (e == d) {
+                    const float thi = 2.f * etac * ((at(ud, op[d]) - udc) * inv_h);
+                    const float tlo = 2.f * etam * ((udc - at(ud, im)) * inv_h);
+                    visc = visc + (thi - tlo) * inv_h;
+                } else {
+                    const float* __restrict__ ue = io.u_s[e];
+                    // edge at (c - e_d/2 - e_e/2): cells c, c-e_d, c-e_e, c-e_d-e_e
+                    const float eta_lo = 0.25f * (etac + etam + eta_of(at(phi, om[e]), pcs) +
+                                                  eta_of(at(phi, im + om[e]), pcs));
+                    const float tlo = eta_lo * ((udc - at(ud, om[e])) * inv_h +
+                                                (at(ue, 0) - at(ue, im)) * inv_h);
+                    // edge at (c - e_d/2 + e_e/2): cells c+e_e, c+e_e-e_d, c, c-e_d
+                    const int iep = op[e], iepm = im + op[e];
+                    const float eta_hi = 0.25f * (eta_of(at(phi, iep), pcs) +
+                                                  eta_of(at(phi, iepm), pcs) + etac + etam);
+                    const float thi = eta_hi * ((at(ud, iep) - udc) * inv_h +
+                                                (at(ue, iep) - at(ue, iepm)) * inv_h);
+                    visc = visc + (thi - tlo) * inv_h;
+                }
+            }
+            // surface tension force at the face
+            const float dphi = (pc - pm) * inv_h;
+            float F;
+            if (ph.force == 0) {
+                F = 0.5f * (at(io.aux, 0) + at(io.aux, im)) * dphi;
+            } else {
+                const float kf = 0.5f * (at(io.aux, 0) + at(io.aux, im));
+                if (ph.force == 1) {
+                    F = sigma * kf * dphi;
+                } else {
+                    const float pf = 0.5f * (pc + pm);
+                    F = 6.f * sigma * kf * pf * (1.f - pf) * dphi;
+                }
+            }
+            const float beta = divq(1.f, 0.5f * (rho_of(pc, pcs) + rho_of(pm, pcs)));
+            ku[d] = -adv + beta * visc + beta * F;
+        }
+
+        if (write_rhs) {
+            io.rhs_phi[idx] = kphi;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) io.rhs_u[d][idx] = ku[d];
+            continue;
+        }
+        // ---------------- RK stage update ----------------
+        const float phin = __ldg(io.phi_n + idx);
+        if (scheme == 1) {  // forward Euler
+            io.phi_out[idx] = phin + cdt * kphi;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) io.u_out[d][idx] = __ldg(io.u_n[d] + idx) + cdt * ku[d];
+            continue;
+        }
+        if (stage < 3) {
+            const float a = stage == 0 ? wdt * kphi : io.acc_phi[idx] + wdt * kphi;
+            io.acc_phi[idx] = a;
+            io.phi_out[idx] = phin + cdt * kphi;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float au = stage == 0 ? wdt * ku[d] : io.acc_u[d][idx] + wdt * ku[d];
+                io.acc_u[d][idx] = au;
+                io.u_out[d][idx] = __ldg(io.u_n[d] + idx) + cdt * ku[d];
+            }
+        } else {
+            io.phi_out[idx] = phin + (io.acc_phi[idx] + wdt * kphi);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                io.u_out[d][idx] = __ldg(io.u_n[d] + idx) + (io.acc_u[d][idx] + wdt * ku[d]);
+        }
+    }
+}
+
 template <typename T, int DIM>
 void launch_stage(const Dims& g, const Phys& ph, const StageIO<T>& io, int stage, int scheme,
                   double wdt, double cdt, int write_rhs, cudaStream_t s) {
+    if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+        int zc = 64;
+        while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
+        dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
+        k_stage3d<<<grid, 256, 0, s>>>(g, ph, io, stage, scheme, float(wdt), float(cdt),
+                                       write_rhs, zc);
+        return;
+    }
     k_stage<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(g, ph, io, stage, scheme,
                                                                           T(wdt), T(cdt), write_rhs);
 }
@@ -422,6 +602,12 @@ k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T
 template <typename T, int DIM>
 void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double* b, RedBuf rb,
                        CGScalars* sc, cudaStream_t s) {
+    if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        if (divergence3d_ok(g)) {
+            launch_divergence3d(g, u, inv_tau, b, rb, sc, s);
+            return;
+        }
+    }
     k_divergence<T, DIM><<<row_grid(g, kThreads, kRedBlocks), kThreads, 0, s>>>(
         g, u[0], u[1], DIM == 3 ? u[2] : u[0], inv_tau, b, rb, sc);
 }
@@ -475,6 +661,12 @@ void launch_correct(const Dims& g, const Phys& ph, const T* phi, const double* c
     const float* f0 = beta32 ? beta32[0] : nullptr;
     const float* f1 = beta32 ? beta32[1] : nullptr;
     const float* f2 = beta32 ? beta32[DIM == 3 ? 2 : 1] : nullptr;
+    if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        if (f0 != nullptr) {
+            launch_correct3d(g, beta32, ustar, p, tau, uout, s);
+            return;
+        }
+    }
     k_correct<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
         g, ph, phi, b0, b1, b2, f0, f1, f2, ustar[0], ustar[1], DIM == 3 ? ustar[2] : ustar[0], p,
         tau, uout[0], uout[1], DIM == 3 ? uout[2] : uout[0]);

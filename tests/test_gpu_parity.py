@@ -294,7 +294,7 @@ def test_tiny_and_odd_grids(pf, n):
     sim.close()
 
 
-@pytest.mark.parametrize("n", [(40, 40, 40), (48, 40, 24), (64, 64, 64)])
+@pytest.mark.parametrize("n", [(40, 40, 40), (48, 40, 24), (64, 64, 64), (42, 40, 24)])
 def test_poisson_mixed_3d_sweeps_converge(pf, n):
     """3D float32 levels use the one-pass tiled red-black sweep (ragged tiles when a
     size is not a multiple of the 32 x 8 tile): the refined solve still reaches a
@@ -316,3 +316,25 @@ def test_poisson_mixed_3d_sweeps_converge(pf, n):
     res = O.apply_poisson(beta_f32(phi, g, po), x, g) - rhs
     assert np.linalg.norm(res) <= 2e-12 * np.linalg.norm(rhs)
     sim.close()
+
+
+def test_poisson_mixed_3d_two_sweeps_per_level(pf):
+    """V(2,2): the out-of-place sweeps alternate their two buffers; the solve
+    converges in fewer inner iterations than with V(1,1)."""
+    n = (48, 40, 24)
+    p = I.small_case(dim=3, n=n[0], rho_in=10.0, rho_out=1.0, precision="mixed",
+                     poisson_rtol=1e-12, poisson_maxit=200)
+    p["n"] = n
+    p["mg_pre"] = p["mg_post"] = 2
+    po = O.params_from(p)
+    g = O.Grid(3, n, p["L"])
+    phi = O.initial_phi(po)
+    rhs = I.noise(g.shape, 13) - 0.5
+    rhs -= rhs.mean()
+    sim = pf.Simulation(p, phi0=phi)
+    x, it, relres, st = sim.poisson_solve(rhs)
+    sim.close()
+    assert st == 0 and relres <= 1e-12
+    assert it <= 12, it
+    res = O.apply_poisson(beta_f32(phi, g, po), x, g) - rhs
+    assert np.linalg.norm(res) <= 2e-12 * np.linalg.norm(rhs)

@@ -172,6 +172,23 @@ class ClockSampler:
 NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 15.55}
 
 
+def deal(items, rank, world):
+    """The instances of rank `rank` of `world`: item i goes to rank i mod world
+    (every item to exactly one rank; no data-path exchange)."""
+    return list(items)[rank::world]
+
+
+def job_time(seconds, dist=None, device=None):
+    """The job's time: the slowest rank's (a MAX all-reduce when distributed)."""
+    if dist is None:
+        return float(seconds)
+    import torch
+
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def algo_bytes_per_cell(cls, dim, w):
     d = dim
     table = {
@@ -271,7 +288,7 @@ def run_batch(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     plist, desc = workload(args.workload)
     total_cells = sum(int(np.prod([c for c in p["n"]])) for p in plist)
-    mine = plist[rank::world]
+    mine = deal(plist, rank, world)
     bat = pf.Batch(mine, nthreads=args.threads)
     bat.step(args.warmup)
 
@@ -291,9 +308,7 @@ def run_batch(args, rank, world, local_rank):
     clk = clocks.stop()
     bat.close()
     if dist is not None:
-        t = torch.tensor([wall], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = float(t.item())
+        wall = job_time(wall, dist, "cuda")
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps({
@@ -357,10 +372,7 @@ def run_ours(args, rank, world, local_rank):
     prof = pf.pf_profile_read(sim.ctx, reset=True)
     pf.pf_profile_enable(sim.ctx, False)
     diag = sim.diagnostics()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time(ms, dist, "cuda")
     ms_step = ms / args.steps
     value = ncell * world * args.steps / (ms / 1e3) / 1e6
     launches = int(sum(v[0] for v in prof.values()))

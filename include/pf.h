@@ -234,6 +234,49 @@ pf_ctx* pf_batch_context(pf_batch* b, int i);
 void pf_batch_destroy(pf_batch* b);
 const char* pf_batch_last_error(const pf_batch* b);
 
+/* Reverse mode (discrete adjoint of pf_step), float64 contexts with the CDI
+ * model (Table 1) and the EB force (Eq. eb_st with Eq. ac_mu). It gives the
+ * gradient of an objective of the state after many steps with respect to the
+ * initial phase field, sigma, the densities and the viscosities; the
+ * checkpoint schedule (which states to keep) is the caller's.
+ *
+ * pf_adjoint_workspace_size: bytes of the adjoint workspace (device memory,
+ * 256-byte aligned, caller-owned) that pf_step_adjoint needs for these
+ * parameters (54 doubles per cell in 2D, 74 in 3D). PF_ERR_INVALID for
+ * unsupported parameters (mixed precision, SB / ISODI, CSF / LCSF).
+ *
+ * pf_step_adjoint: transposed Jacobian of one step applied to a cotangent.
+ *  state_n: the state at the start of the step in the pf_get_state layout
+ *    (host or device), e.g. a checkpoint; the step is recomputed from it, and
+ *    on return the context holds the state after the step.
+ *  lam: device float64 array of (1 + dim) * nx*ny*nz entries, components back
+ *    to back (phi, u, v[, w]); on entry the cotangent dJ/d(state after the
+ *    step), on return dJ/d(state at the start of the step).
+ *  gparam: device float64[5] or NULL; dJ/d(sigma, rho_in, rho_out, mu_in,
+ *    mu_out) of this step is ADDED to it.
+ *  The transpose follows the forward arithmetic: the stage right-hand sides
+ *  (normals, CDI flux, chemical potential, EB force, advection, viscous
+ *  stress, face densities) and each projection u = u* - tau beta G p with
+ *  A p = -D u* / tau, whose transpose is mu = lam + G A^+ D(beta lam) (one
+ *  Poisson solve with the same operator) plus the density term
+ *  (tau/2) sum_f mu_f beta_f^2 (G p)_f through rho(phi). Gamma: fixed when
+ *  gamma_fixed > 0; otherwise max(gamma_min, max|u^n|) is differentiated at
+ *  the first face (lowest index, x faces first) that attains the maximum.
+ *  clip(phi, 0, 1) has derivative 1 strictly inside (0, 1) and 0 elsewhere.
+ *  The Poisson solves use poisson_rtol. Synchronises the stream.
+ *
+ * pf_objective: J = w_ke KE + (w_shape / 2) sum (phi - phi_target)^2 dV of the
+ *  current state (KE as in pf_diagnostics; phi_target a device float64 array
+ *  or NULL for no misfit term). J is written to host memory; grad (device,
+ *  (1 + dim) * nx*ny*nz doubles, layout of lam) receives dJ/d(phi, u); gparam
+ *  (device float64[5] or NULL) receives dJ/d(rho_in, rho_out) added to its
+ *  entries 1 and 2. Synchronises the stream. */
+pf_status pf_adjoint_workspace_size(const pf_params* prm, size_t* bytes);
+pf_status pf_step_adjoint(pf_ctx* ctx, void* adj_workspace, size_t adj_bytes, const void* state_n,
+                          double* lam, double* gparam);
+pf_status pf_objective(pf_ctx* ctx, const double* phi_target, double w_ke, double w_shape,
+                       double* J, double* grad, double* gparam);
+
 /* Wait for all work of the context and return the latched device status. */
 pf_status pf_sync(pf_ctx* ctx);
 

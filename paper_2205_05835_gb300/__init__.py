@@ -118,6 +118,19 @@ class Simulation:
     def state_bytes(self) -> int:
         return pf_state_bytes(self.ctx)
 
+    def state_tensor(self):
+        """The raw state (pf_get_state layout) in a new device uint8 tensor."""
+        import torch
+
+        t = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.workspace.device)
+        pf_get_state(self.ctx, t.data_ptr())
+        return t
+
+    def load_state(self, t) -> None:
+        """Restore a state taken by state_tensor (host or device tensor)."""
+        assert t.numel() == self.state_bytes() and t.is_contiguous()
+        pf_set_state(self.ctx, t.data_ptr())
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             pf_destroy(self.ctx)

@@ -28,7 +28,8 @@ SYMBOLS = ["pf_workspace_size", "pf_init", "pf_step", "pf_project", "pf_diagnost
            "pf_profile_enable", "pf_profile_read", "pf_poisson_solve_static",
            "pf_batch_workspace_size", "pf_batch_init", "pf_batch_step", "pf_batch_step_each",
            "pf_batch_size",
-           "pf_batch_context", "pf_batch_destroy", "pf_batch_last_error"]
+           "pf_batch_context", "pf_batch_destroy", "pf_batch_last_error",
+           "pf_adjoint_workspace_size", "pf_step_adjoint", "pf_objective"]
 
 
 class pf_params(ctypes.Structure):
@@ -108,6 +109,9 @@ def _load():
         "pf_batch_context": (vp, [vp, i32]),
         "pf_batch_destroy": (None, [vp]),
         "pf_batch_last_error": (ctypes.c_char_p, [vp]),
+        "pf_adjoint_workspace_size": (i32, [P(pf_params), P(sz)]),
+        "pf_step_adjoint": (i32, [vp, vp, sz, vp, vp, vp]),
+        "pf_objective": (i32, [vp, vp, f64, f64, P(f64), vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -263,6 +267,24 @@ def pf_batch_context(b, i: int):
 
 def pf_batch_destroy(b):
     LIB.pf_batch_destroy(b)
+
+
+def pf_adjoint_workspace_size(params: pf_params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(LIB.pf_adjoint_workspace_size(ctypes.byref(params), ctypes.byref(n)))
+    return n.value
+
+
+def pf_step_adjoint(ctx, workspace: int, workspace_bytes: int, state_n: int, lam: int,
+                    gparam: int | None):
+    return _check(LIB.pf_step_adjoint(ctx, workspace, workspace_bytes, state_n, lam, gparam), ctx)
+
+
+def pf_objective(ctx, phi_target: int | None, w_ke: float, w_shape: float, grad: int,
+                 gparam: int | None) -> float:
+    J = ctypes.c_double(0.0)
+    _check(LIB.pf_objective(ctx, phi_target, w_ke, w_shape, ctypes.byref(J), grad, gparam), ctx)
+    return J.value
 
 
 def pf_last_error(ctx=None) -> str:

@@ -57,6 +57,11 @@ struct Impl {
     virtual pf_status eval_rhs(double gamma, double* kphi, double* ku) = 0;
     virtual pf_status poisson_solve(const double* rhs, double* x, int* iters, double* relres) = 0;
     virtual pf_status sync() = 0;
+    virtual size_t adjoint_bytes() = 0;
+    virtual pf_status step_adjoint(void* aws, size_t abytes, const void* state_n, double* lam,
+                                   double* gparam) = 0;
+    virtual pf_status objective(const double* target, double w_ke, double w_shape, double* J,
+                                double* grad, double* gparam) = 0;
     Prof prof;
 };
 
@@ -186,6 +191,15 @@ struct ImplT final : Impl {
     double* h_scalar = nullptr;
     long long nstep = 0;
     double time = 0.0;
+    // reverse mode: stage record of one step (phi_0..phi_3, phi^{n+1}; u_0..u_3;
+    // the pressures of the four projections) and an explicit solve target
+    struct Tape {
+        T* phi[5];
+        T* u[4][3];
+        double* p[4];
+    };
+    Tape* tape = nullptr;
+    double* xsolve = nullptr;
     int last_iters = 0, max_iters = 0;
     double last_relres = 0.0, last_gamma = 0.0;
     int host_status = 0;
@@ -464,7 +478,7 @@ struct ImplT final : Impl {
         io.diag = diag64;
         io.b = b;
         io.sign = sign;
-        io.x = p;
+        io.x = xsolve ? xsolve : p;
         io.r = rT;
         io.z = z;
         io.p[0] = pd[0];
@@ -594,6 +608,10 @@ struct ImplT final : Impl {
             io.u_out[d] = uStar[d];
             io.nrm[d] = nrm[d];
         }
+        if (tape) {
+            tape_copy(tape->phi[0], phiN);
+            for (int d = 0; d < DIM; ++d) tape_copy(tape->u[0][d], uN[d]);
+        }
         if (prm.scheme == PF_FE) {
             io.phi_s = phiN;
             for (int d = 0; d < 3; ++d) io.u_s[d] = uN[d];
@@ -605,6 +623,10 @@ struct ImplT final : Impl {
             launch_stage<T, DIM>(g, ph, io, 0, 1, dt, dt, 0, st);
             prof.end();
             pf_status s = do_project(phiA, uStar, dt, uN);
+            if (tape) {
+                tape_copy(tape->phi[1], phiA);
+                tape_copy(tape->p[0], p);
+            }
             T* t = phiN;
             phiN = phiA;
             phiA = t;
@@ -626,8 +648,19 @@ struct ImplT final : Impl {
             prof.end();
             pf_status ps = do_project(phout[s], uStar, cdt, s < 3 ? uS : uN);
             if (ps != PF_OK) return ps;
+            if (tape) {
+                tape_copy(tape->phi[s + 1], phout[s]);
+                if (s < 3)
+                    for (int d = 0; d < DIM; ++d) tape_copy(tape->u[s + 1][d], uS[d]);
+                tape_copy(tape->p[s], p);
+            }
         }
         return PF_OK;
+    }
+
+    template <typename Q>
+    void tape_copy(Q* dst, const Q* src) {
+        cudaMemcpyAsync(dst, src, (size_t)g.ncell * sizeof(Q), cudaMemcpyDeviceToDevice, st);
     }
 
     pf_status step(int nsteps) override {
@@ -830,6 +863,239 @@ struct ImplT final : Impl {
         CK(cudaMemcpyAsync(x, b, bytes, cudaMemcpyDefault, st));
         CK(cudaStreamSynchronize(st));
         return s;
+    }
+
+    // ---------------- reverse mode (float64, CDI + EB) ----------------
+    // Adjoint workspace: the stage record of one step and the cotangent arrays.
+    struct AdjWS {
+        Tape tp;
+        double *Lphi, *Lu[3];        // cotangent of the step's initial state (accumulated)
+        double *P4phi, *P4u[3];      // cotangent of phi^{n+1} and of the last u* (kept)
+        double *prevPhi, *prevU[3];  // cotangent of phi_{s+1}, u*_{s+1} of the stage above
+        double *kphi, *ku[3];        // cotangent of the stage right-hand sides
+        double *sphi, *su[3];        // transposed right-hand side outputs
+        double *mus[3];              // projection transpose output
+        double *v[3], *w;            // beta lam and A^+ D(beta lam)
+        AdjRhsIO rio;
+        double* acc;                 // [8] parameter and Gamma sums of the step
+    };
+
+    bool adjoint_supported(std::string& why) const {
+        if (sizeof(T) != sizeof(double)) { why = "the adjoint needs precision PF_FP64"; return false; }
+        if (prm.model != PF_CDI || prm.force != PF_FORCE_EB) {
+            why = "the adjoint supports the CDI model with the EB force";
+            return false;
+        }
+        return true;
+    }
+
+    void carve_adj(Carver& cv, AdjWS& a) {
+        const size_t n = g.ncell;
+        memset(&a, 0, sizeof(a));
+        for (int s = 0; s < 5; ++s) a.tp.phi[s] = cv.take<T>(n);
+        for (int s = 0; s < 4; ++s)
+            for (int d = 0; d < DIM; ++d) a.tp.u[s][d] = cv.take<T>(n);
+        for (int s = 0; s < 4; ++s) a.tp.p[s] = cv.take<double>(n);
+        a.Lphi = cv.take<double>(n);
+        a.P4phi = cv.take<double>(n);
+        a.prevPhi = cv.take<double>(n);
+        a.kphi = cv.take<double>(n);
+        a.sphi = cv.take<double>(n);
+        a.w = cv.take<double>(n);
+        for (int d = 0; d < DIM; ++d) {
+            a.Lu[d] = cv.take<double>(n);
+            a.P4u[d] = cv.take<double>(n);
+            a.prevU[d] = cv.take<double>(n);
+            a.ku[d] = cv.take<double>(n);
+            a.su[d] = cv.take<double>(n);
+            a.mus[d] = cv.take<double>(n);
+            a.v[d] = cv.take<double>(n);
+            a.rio.lo[d] = cv.take<double>(n);
+            a.rio.hi[d] = cv.take<double>(n);
+            a.rio.nfb[d] = cv.take<double>(n);
+            a.rio.mufb[d] = cv.take<double>(n);
+            a.rio.rhofb[d] = cv.take<double>(n);
+            a.rio.W[d] = cv.take<double>(n);
+            a.rio.gbar[d] = cv.take<double>(n);
+        }
+        const int npair = DIM == 3 ? 3 : 1;
+        for (int q = 0; q < npair; ++q) a.rio.te[q] = cv.take<double>(n);
+        a.rio.mubar = cv.take<double>(n);
+        a.rio.phibar_tmp = cv.take<double>(n);
+        a.acc = cv.take<double>(8);
+    }
+
+    size_t adjoint_bytes() override {
+        AdjWS a;
+        Carver cv{nullptr};
+        carve_adj(cv, a);
+        return cv.off;
+    }
+
+    // transposed right-hand side of stage (phi_s, u_s) applied to (kphi, ku):
+    // sphi, su written; parameter and Gamma sums added to acc
+    void adj_rhs(AdjWS& a, const double* phis, double* const* us) {
+        launch_cell_pass<T, DIM>(g, ph, reinterpret_cast<const T*>(phis), nrm[0], nrm[1], nrm[2],
+                                 aux, st);
+        AdjRhsIO io = a.rio;
+        io.phi = phis;
+        for (int d = 0; d < 3; ++d) {
+            io.u[d] = d < DIM ? us[d] : nullptr;
+            io.nrm[d] = d < DIM ? reinterpret_cast<const double*>(nrm[d]) : nullptr;
+            io.kbar_u[d] = d < DIM ? a.ku[d] : nullptr;
+            io.ubar[d] = d < DIM ? a.su[d] : nullptr;
+        }
+        io.mu = reinterpret_cast<const double*>(aux);
+        io.gamma = gamma;
+        io.kbar_phi = a.kphi;
+        io.phibar = a.sphi;
+        io.acc = a.acc;
+        launch_adj_rhs<DIM>(g, ph, io, rb, st);
+    }
+
+    // transposed projection u = P(phi) u* (pressure p, time factor tau) applied
+    // to lam: mu = P^T lam written, the density part added to phibar
+    pf_status adj_project(AdjWS& a, const double* phis, const double* pr, double tau,
+                          double* const* lam, double* const* mu, double* phibar) {
+        AdjProjIO io;
+        memset(&io, 0, sizeof(io));
+        io.phi = phis;
+        io.p = pr;
+        for (int d = 0; d < DIM; ++d) {
+            io.lam[d] = lam[d];
+            io.v[d] = a.v[d];
+            io.mu[d] = mu[d];
+        }
+        io.w = a.w;
+        io.tau = tau;
+        io.phibar = phibar;
+        io.acc = a.acc;
+        launch_adj_beta_lam<DIM>(g, ph, io, st);
+        const T* vc[3] = {reinterpret_cast<const T*>(a.v[0]), reinterpret_cast<const T*>(a.v[1]),
+                          reinterpret_cast<const T*>(DIM == 3 ? a.v[2] : a.v[0])};
+        launch_divergence<T, DIM>(g, vc, 1.0, b, rb, sc, st);
+        // A w = D(beta lam) - mean, from a zero start (a zero right-hand side
+        // then ends the solve at once)
+        CK(cudaMemsetAsync(a.w, 0, (size_t)g.ncell * sizeof(double), st));
+        xsolve = a.w;
+        pf_status s = solve(reinterpret_cast<const T*>(phis), 1.0);
+        xsolve = nullptr;
+        if (s != PF_OK) return s;
+        launch_adj_proj_post<DIM>(g, ph, io, rb, st);
+        return PF_OK;
+    }
+
+    pf_status step_adjoint(void* aws, size_t abytes, const void* state_n, double* lam,
+                           double* gparam) override {
+        std::string why;
+        if (!adjoint_supported(why)) { err = why; return PF_ERR_INVALID; }
+        if (!aws || !state_n || !lam) { err = "NULL pointer"; return PF_ERR_INVALID; }
+        if ((reinterpret_cast<uintptr_t>(aws) % kAlign) != 0 || abytes < adjoint_bytes()) {
+            err = "adjoint workspace NULL, not 256-byte aligned or smaller than pf_adjoint_workspace_size";
+            return PF_ERR_WORKSPACE;
+        }
+        AdjWS a;
+        Carver cv{static_cast<char*>(aws)};
+        carve_adj(cv, a);
+        const size_t n = g.ncell;
+        const size_t nb = n * sizeof(double);
+        double* lam_phi = lam;
+        double* lam_u[3] = {lam + n, lam + 2 * n, DIM == 3 ? lam + 3 * n : nullptr};
+        // forward recomputation of the step with its stage record
+        pf_status s = set_state(state_n);
+        if (s != PF_OK) return s;
+        tape = &a.tp;
+        s = one_step();
+        tape = nullptr;
+        if (s != PF_OK) return s;
+        ++nstep;
+        time += prm.dt;
+        CK(cudaMemsetAsync(a.acc, 0, 8 * sizeof(double), st));
+        const double dt = prm.dt;
+        double* tphi[5];
+        double* tu[4][3];
+        for (int q = 0; q < 5; ++q) tphi[q] = reinterpret_cast<double*>(a.tp.phi[q]);
+        for (int q = 0; q < 4; ++q)
+            for (int d = 0; d < 3; ++d)
+                tu[q][d] = d < DIM ? reinterpret_cast<double*>(a.tp.u[q][d]) : nullptr;
+        // last projection: u^{n+1} = P(phi^{n+1}) u*
+        const int last = prm.scheme == PF_FE ? 1 : 4;
+        CK(cudaMemcpyAsync(a.P4phi, lam_phi, nb, cudaMemcpyDeviceToDevice, st));
+        s = adj_project(a, tphi[last], a.tp.p[last - 1], dt, lam_u, a.P4u, a.P4phi);
+        if (s != PF_OK) return s;
+        if (prm.scheme == PF_FE) {
+            launch_axpby((int)n, dt, a.P4phi, 0.0, nullptr, a.kphi, st);
+            for (int d = 0; d < DIM; ++d) launch_axpby((int)n, dt, a.P4u[d], 0.0, nullptr, a.ku[d], st);
+            adj_rhs(a, tphi[0], tu[0]);
+            launch_axpby((int)n, 1.0, a.P4phi, 1.0, a.sphi, a.Lphi, st);
+            for (int d = 0; d < DIM; ++d) launch_axpby((int)n, 1.0, a.P4u[d], 1.0, a.su[d], a.Lu[d], st);
+        } else {
+            CK(cudaMemcpyAsync(a.Lphi, a.P4phi, nb, cudaMemcpyDeviceToDevice, st));
+            for (int d = 0; d < DIM; ++d)
+                CK(cudaMemcpyAsync(a.Lu[d], a.P4u[d], nb, cudaMemcpyDeviceToDevice, st));
+            for (int sg = 3; sg >= 0; --sg) {
+                // cotangent of k_s: from phi^{n+1} / u^{n+1} (weight w_s) and from
+                // stage s + 1 (phi_{s+1} = phi^n + c_{s+1} dt k_s)
+                const double wdt = kRK4W[sg] * dt;
+                const double cdt_up = sg < 3 ? kRK4C[sg + 1] * dt : 0.0;
+                launch_axpby((int)n, wdt, a.P4phi, cdt_up, sg < 3 ? a.prevPhi : nullptr, a.kphi, st);
+                for (int d = 0; d < DIM; ++d)
+                    launch_axpby((int)n, wdt, a.P4u[d], cdt_up, sg < 3 ? a.prevU[d] : nullptr,
+                                 a.ku[d], st);
+                adj_rhs(a, tphi[sg], tu[sg]);
+                if (sg >= 1) {
+                    // u_s = P(phi_s) u*_s with tau = c_s dt
+                    s = adj_project(a, tphi[sg], a.tp.p[sg - 1], kRK4C[sg] * dt, a.su, a.mus,
+                                    a.sphi);
+                    if (s != PF_OK) return s;
+                    launch_addto((int)n, a.sphi, a.Lphi, st);
+                    CK(cudaMemcpyAsync(a.prevPhi, a.sphi, nb, cudaMemcpyDeviceToDevice, st));
+                    for (int d = 0; d < DIM; ++d) {
+                        launch_addto((int)n, a.mus[d], a.Lu[d], st);
+                        CK(cudaMemcpyAsync(a.prevU[d], a.mus[d], nb, cudaMemcpyDeviceToDevice, st));
+                    }
+                } else {
+                    launch_addto((int)n, a.sphi, a.Lphi, st);
+                    for (int d = 0; d < DIM; ++d) launch_addto((int)n, a.su[d], a.Lu[d], st);
+                }
+            }
+        }
+        // Gamma = max(gamma_min, max |u^n|) (unless fixed)
+        if (!(prm.gamma_fixed > 0.0)) {
+            const double* u0c[3] = {tu[0][0], tu[0][1], DIM == 3 ? tu[0][2] : tu[0][0]};
+            launch_adj_gamma<DIM>(g, u0c, gamma, prm.gamma_min, a.acc, a.Lu, rb, st);
+        }
+        CK(cudaMemcpyAsync(lam_phi, a.Lphi, nb, cudaMemcpyDeviceToDevice, st));
+        for (int d = 0; d < DIM; ++d)
+            CK(cudaMemcpyAsync(lam_u[d], a.Lu[d], nb, cudaMemcpyDeviceToDevice, st));
+        if (gparam) launch_add_small(5, a.acc, gparam, st);
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        return PF_OK;
+    }
+
+    pf_status objective(const double* target, double w_ke, double w_shape, double* J,
+                        double* grad, double* gparam) override {
+        if (sizeof(T) != sizeof(double)) {
+            err = "the objective gradient needs precision PF_FP64";
+            return PF_ERR_INVALID;
+        }
+        if (!J || !grad) { err = "NULL pointer"; return PF_ERR_INVALID; }
+        const size_t n = g.ncell;
+        const double* uc[3] = {reinterpret_cast<const double*>(uN[0]),
+                               reinterpret_cast<const double*>(uN[1]),
+                               DIM == 3 ? reinterpret_cast<const double*>(uN[2]) : nullptr};
+        double* gu[3] = {grad + n, grad + 2 * n, DIM == 3 ? grad + 3 * n : nullptr};
+        // parameter sums go to dsum[1..2] when gparam is NULL
+        CK(cudaMemsetAsync(dsum, 0, 4 * sizeof(double), st));
+        double* acc = gparam ? gparam : dsum;
+        launch_objective<DIM>(g, ph, reinterpret_cast<const double*>(phiN), uc, target, w_ke,
+                              w_shape, grad, gu, rb, dsum + 3, acc, st);
+        CK(cudaMemcpyAsync(h_scalar + 5, dsum + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        *J = h_scalar[5];
+        return PF_OK;
     }
 
     pf_status sync() override {
@@ -1051,6 +1317,35 @@ pf_status pf_poisson_solve(pf_ctx* ctx, const double* rhs, double* x, int* iters
                            double* relres) {
     if (!ctx) return PF_ERR_INVALID;
     return ctx->impl->poisson_solve(rhs, x, iters, relres);
+}
+
+pf_status pf_adjoint_workspace_size(const pf_params* prm, size_t* bytes) {
+    std::string why;
+    pf_status s = validate(prm, why);
+    if (s != PF_OK) { g_init_error = why; return s; }
+    if (!bytes) { g_init_error = "bytes is NULL"; return PF_ERR_INVALID; }
+    if (prm->precision != PF_FP64 || prm->model != PF_CDI || prm->force != PF_FORCE_EB) {
+        g_init_error = "the adjoint supports precision PF_FP64 with the CDI model and the EB force";
+        return PF_ERR_INVALID;
+    }
+    std::string err;
+    Impl* im = make_impl(*prm, nullptr, err);
+    if (!im) return PF_ERR_INVALID;
+    *bytes = im->adjoint_bytes();
+    delete im;
+    return PF_OK;
+}
+
+pf_status pf_step_adjoint(pf_ctx* ctx, void* adj_workspace, size_t adj_bytes, const void* state_n,
+                          double* lam, double* gparam) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->step_adjoint(adj_workspace, adj_bytes, state_n, lam, gparam);
+}
+
+pf_status pf_objective(pf_ctx* ctx, const double* phi_target, double w_ke, double w_shape,
+                       double* J, double* grad, double* gparam) {
+    if (!ctx) return PF_ERR_INVALID;
+    return ctx->impl->objective(phi_target, w_ke, w_shape, J, grad, gparam);
 }
 
 pf_status pf_profile_enable(pf_ctx* ctx, int enable) {

@@ -288,6 +288,61 @@ void launch_in_update(const Dims& g, const SolveIO<T, DIM>& io, int cur, int fir
                       CGScalars* sc, cudaStream_t s);
 void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s);
 
+// ---- reverse mode (float64; pf_adjoint.cu) ----
+// Arrays of the transposed right-hand side of one stage (CDI + EB force).
+struct AdjRhsIO {
+    const double* phi;        // stage phase field
+    const double* u[3];       // stage velocity
+    const double* nrm[3];     // cell normals of phi (forward cell pass)
+    const double* mu;         // chemical potential of phi (forward cell pass)
+    const double* gamma;      // device scalar Gamma of the step
+    const double* kbar_phi;   // cotangent of the phase-field rhs (cells)
+    const double* kbar_u[3];  // cotangent of the momentum rhs (faces)
+    double* lo[3];            // phi cotangent a d-face sends to its high cell
+    double* hi[3];            // ... and to its low cell
+    double* nfb[3];           // face-normal cotangents
+    double* mufb[3];          // face chemical-potential cotangents
+    double* rhofb[3];         // face-density cotangents
+    double* W[3];             // b_d beta_d (cotangent of visc + force)
+    double* te[3];            // edge stress cotangents, pairs (0,1), (0,2), (1,2)
+    double* gbar[3];          // cotangent of the central gradient (cells)
+    double* mubar;            // cotangent of mu (cells)
+    double* phibar_tmp;       // partial phi cotangent
+    double* phibar;           // out: phi cotangent (written)
+    double* ubar[3];          // out: u cotangent (written)
+    double* acc;              // [6] sums: sigma, rho_in, rho_out, mu_in, mu_out, Gamma
+};
+// Arrays of the transposed projection u = u* - tau beta G p.
+struct AdjProjIO {
+    const double* phi;        // phase field of the projection's density
+    const double* p;          // its pressure
+    const double* lam[3];     // cotangent of the projected velocity (faces)
+    double* v[3];             // scratch: beta lam
+    const double* w;          // A^+ D(beta lam)
+    double tau;
+    double* mu[3];            // out: cotangent of u* (faces), written
+    double* phibar;           // phi cotangent (density part added)
+    double* acc;              // [6] parameter sums
+};
+template <int DIM>
+void launch_adj_rhs(const Dims& g, const Phys& ph, const AdjRhsIO& io, RedBuf rb, cudaStream_t s);
+template <int DIM>
+void launch_adj_beta_lam(const Dims& g, const Phys& ph, const AdjProjIO& io, cudaStream_t s);
+template <int DIM>
+void launch_adj_proj_post(const Dims& g, const Phys& ph, const AdjProjIO& io, RedBuf rb,
+                          cudaStream_t s);
+template <int DIM>
+void launch_objective(const Dims& g, const Phys& ph, const double* phi, const double* const* u,
+                      const double* target, double w_ke, double w_shape, double* gphi,
+                      double* const* gu, RedBuf rb, double* J, double* acc, cudaStream_t s);
+template <int DIM>
+void launch_adj_gamma(const Dims& g, const double* const* u, const double* gamma, double gamma_min,
+                      const double* acc, double* const* lam_u, RedBuf rb, cudaStream_t s);
+void launch_axpby(int n, double alpha, const double* x, double beta, const double* y, double* out,
+                  cudaStream_t s);
+void launch_addto(int n, const double* x, double* y, cudaStream_t s);
+void launch_add_small(int k, const double* src, double* dst, cudaStream_t s);
+
 }  // namespace pf
 
 struct pf_ctx;

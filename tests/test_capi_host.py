@@ -128,3 +128,35 @@ def test_study_instances_follow_section_3_1():
         assert p["rho_in"] == p["rho_out"] == 300 and 2 * p["R"] == 0.4
         assert abs(math.sqrt(32) * p["eps"] ** 1.5 - 1.0 / n) < 1e-12
     assert abs(S.eps_of("eps", 32) - 1 / 32) < 1e-15 and S.eps_of("h", 256) == 1 / 32
+
+
+def test_adjoint_workspace_and_validation(pf):
+    """pf_adjoint_workspace_size: float64 CDI + EB only, size linear in the cells."""
+    import pf_inputs as I
+
+    p = pf.make_params(I.small_case(dim=2, n=32))
+    b32 = pf.B.pf_adjoint_workspace_size(p)
+    p64 = pf.make_params(I.small_case(dim=2, n=64))
+    b64 = pf.B.pf_adjoint_workspace_size(p64)
+    # 54 doubles per cell in 2D (plus 256-byte alignment of each array)
+    assert 64 * 64 * 8 * 54 <= b64 <= 64 * 64 * 8 * 54 + 256 * 60
+    assert b32 < b64
+    for bad in (dict(precision="mixed"), dict(model="sb"), dict(force="csf")):
+        q = pf.make_params(I.small_case(dim=2, n=32, **bad))
+        with pytest.raises(pf.PFError) as e:
+            pf.B.pf_adjoint_workspace_size(q)
+        assert e.value.status == pf.B.PF_ERR_INVALID
+
+
+def test_checkpoint_segments_cover_the_run(pf):
+    from paper_2205_05835_gb300.adjoint import checkpoint_segments
+
+    assert checkpoint_segments(500, 25) == [(s, 25) for s in range(0, 500, 25)]
+    assert checkpoint_segments(10, 4) == [(0, 4), (4, 4), (8, 2)]
+    assert checkpoint_segments(0, 3) == []
+    for n, k in ((1, 1), (7, 3), (12, 5), (13, 13), (5, 9)):
+        segs = checkpoint_segments(n, k)
+        assert sum(c for _, c in segs) == n
+        assert all(b == a + c for (a, c), (b, _) in zip(segs, segs[1:]))
+    with pytest.raises(ValueError):
+        checkpoint_segments(5, 0)

@@ -176,8 +176,6 @@ struct ImplT final : Impl {
     double *p, *b;
     double* beta64[3];   // float64 face coefficients (float64 path only)
     float* beta32[3] = {nullptr, nullptr, nullptr};  // float32 face coefficients (mixed path)
-    double* wide64[3] = {nullptr, nullptr, nullptr};  // beta32 in float64 (expanded residual)
-    double* diag64 = nullptr;                         // per-cell sum of beta32
     T *rT, *z, *pd[2], *qT, *eT;
     MGHier<T> H;
     RedBuf rb;
@@ -263,14 +261,34 @@ struct ImplT final : Impl {
         if (h_scalar) cudaFreeHost(h_scalar);
     }
 
-    // Mixed path: the float64 residual in the expanded form, whose rounding
-    // floor (about 2.5e-17 N^2 of ||f|| for a smooth solution) stays at least
-    // ten times below the requested tolerance.
-    bool expanded_residual() const {
-        if (sizeof(T) != sizeof(float)) return false;
-        double nmax = g.nx > g.ny ? g.nx : g.ny;
-        if (g.nz > nmax) nmax = g.nz;
-        return prm.poisson_rtol >= 2.5e-16 * nmax * nmax;
+    // The mixed path keeps the pressure p and the projection's right-hand side
+    // b as double-floats: n float hi parts, then n float lo parts, in the 8 n
+    // bytes of each array (the float64 path keeps them float64).
+    static constexpr bool kDF = sizeof(T) == sizeof(float);
+    float* df_hi(double* a) { return reinterpret_cast<float*>(a); }
+    float* df_lo(double* a) { return reinterpret_cast<float*>(a) + g.ncell; }
+    // float64 array src (device) -> double-float planes of dst, through the CG
+    // direction buffers (free outside a solve); src and dst may be the same array
+    void to_df(const double* src, double* dst) {
+        float* t0 = reinterpret_cast<float*>(pd[0]);
+        float* t1 = reinterpret_cast<float*>(pd[1]);
+        launch_double_to_df(src, t0, t1, g.ncell, st);
+        const size_t nb = (size_t)g.ncell * sizeof(float);
+        cudaMemcpyAsync(df_hi(dst), t0, nb, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(df_lo(dst), t1, nb, cudaMemcpyDeviceToDevice, st);
+    }
+    // p with zero mean as float64 into dst (device), through b
+    void pressure_out(double* dst) {
+        const int n = g.ncell;
+        if (kDF) {
+            launch_df_to_double(df_hi(p), df_lo(p), b, n, st);
+            launch_sum(n, b, rb, dsum, st);
+            launch_sub_mean(b, n, dsum, 1.0 / (double)n, st);
+        } else {
+            launch_sum(n, p, rb, dsum, st);
+            launch_convert_out<double>(p, b, n, 0.0, dsum, 1.0 / (double)n, st);
+        }
+        cudaMemcpyAsync(dst, b, (size_t)n * sizeof(double), cudaMemcpyDefault, st);
     }
 
     void carve(Carver& cv) override {
@@ -299,10 +317,6 @@ struct ImplT final : Impl {
             beta64[d] = (sizeof(T) == sizeof(double) && d < DIM) ? cv.take<double>(n) : nullptr;
         for (int d = 0; d < 3; ++d)
             beta32[d] = (sizeof(T) == sizeof(float) && d < DIM) ? cv.take<float>(n) : nullptr;
-        if (expanded_residual()) {
-            for (int d = 0; d < DIM; ++d) wide64[d] = cv.take<double>(n);
-            diag64 = cv.take<double>(n);
-        }
         H.lev[0].x = z;
         H.lev[0].f = rT;
         for (int d = 0; d < 3; ++d)
@@ -374,8 +388,13 @@ struct ImplT final : Impl {
         CK(cudaMemcpyAsync(sc, &s0, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
         launch_convert_in<T>(phi_in, phiN, (int)n, st);
         CK(cudaMemcpyAsync(b, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (kDF) {
+            launch_double_to_df(x, df_hi(p), df_lo(p), (int)n, st);
+        } else {
+            CK(cudaMemcpyAsync(p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
         launch_sum((int)n, b, rb, dsum, st);
+        if (kDF) to_df(b, b);
         double sum_b = 0.0;
         CK(cudaMemcpyAsync(&sum_b, dsum, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -388,9 +407,7 @@ struct ImplT final : Impl {
             h_sc = nullptr;
             return s;
         }
-        launch_sum((int)n, p, rb, dsum, st);
-        launch_convert_out<double>(p, b, (int)n, 0.0, dsum, 1.0 / (double)n, st);
-        CK(cudaMemcpyAsync(x, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        pressure_out(x);
         CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
         h_sc = nullptr;
@@ -474,8 +491,6 @@ struct ImplT final : Impl {
         io.phi = phi;
         for (int d = 0; d < 3; ++d) io.beta64[d] = sizeof(T) == sizeof(double) ? beta64[d] : nullptr;
         for (int d = 0; d < 3; ++d) io.beta32[d] = sizeof(T) == sizeof(float) ? beta32[d] : nullptr;
-        for (int d = 0; d < 3; ++d) io.wide[d] = wide64[d];
-        io.diag = diag64;
         io.b = b;
         io.sign = sign;
         io.x = xsolve ? xsolve : p;
@@ -511,8 +526,7 @@ struct ImplT final : Impl {
             prof.end();
         } else if (beta32[0] != nullptr) {
             prof.begin(KC_BETA0);
-            launch_beta0_32<DIM>(g, ph, reinterpret_cast<const float*>(phi), beta32, wide64, diag64,
-                                 st);
+            launch_beta0_32<DIM>(g, ph, reinterpret_cast<const float*>(phi), beta32, st);
             prof.end();
         }
         prof.begin(KC_COARSEN);
@@ -735,14 +749,13 @@ struct ImplT final : Impl {
         if (!dst) { err = "dst is NULL"; return PF_ERR_INVALID; }
         const size_t bytes = (size_t)g.ncell * sizeof(double);
         if (f == PF_FIELD_P) {
-            launch_sum(g.ncell, p, rb, dsum, st);
-            launch_convert_out<double>(p, b, g.ncell, 0.0, dsum, 1.0 / g.ncell, st);
+            pressure_out(dst);
         } else {
             T* src = field_ptr(f);
             if (!src) { err = "bad field id"; return PF_ERR_INVALID; }
             launch_convert_out<T>(src, b, g.ncell, 0.0, nullptr, 0.0, st);
+            CK(cudaMemcpyAsync(dst, b, bytes, cudaMemcpyDefault, st));
         }
-        CK(cudaMemcpyAsync(dst, b, bytes, cudaMemcpyDefault, st));
         CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
         return PF_OK;
@@ -753,7 +766,10 @@ struct ImplT final : Impl {
         const size_t bytes = (size_t)g.ncell * sizeof(double);
         CK(cudaMemcpyAsync(b, src, bytes, cudaMemcpyDefault, st));
         if (f == PF_FIELD_P) {
-            CK(cudaMemcpyAsync(p, b, bytes, cudaMemcpyDeviceToDevice, st));
+            if (kDF)
+                launch_double_to_df(b, df_hi(p), df_lo(p), g.ncell, st);
+            else
+                CK(cudaMemcpyAsync(p, b, bytes, cudaMemcpyDeviceToDevice, st));
         } else {
             T* dstp = field_ptr(f);
             if (!dstp) { err = "bad field id"; return PF_ERR_INVALID; }
@@ -846,21 +862,25 @@ struct ImplT final : Impl {
     pf_status poisson_solve(const double* rhs, double* x, int* iters, double* relres) override {
         if (!rhs || !x) { err = "NULL pointer"; return PF_ERR_INVALID; }
         const size_t bytes = (size_t)g.ncell * sizeof(double);
+        if (kDF) {
+            CK(cudaMemcpyAsync(b, x, bytes, cudaMemcpyDefault, st));
+            launch_double_to_df(b, df_hi(p), df_lo(p), g.ncell, st);
+        } else {
+            CK(cudaMemcpyAsync(p, x, bytes, cudaMemcpyDefault, st));
+        }
         CK(cudaMemcpyAsync(b, rhs, bytes, cudaMemcpyDefault, st));
-        CK(cudaMemcpyAsync(p, x, bytes, cudaMemcpyDefault, st));
         launch_sum(g.ncell, b, rb, dsum, st);
         // mean_b = sum / n, written into the scalars
         CK(cudaMemcpyAsync(h_scalar + 3, dsum, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         h_scalar[4] = h_scalar[3] / g.ncell;
         CK(cudaMemcpyAsync(&sc->mean_b, h_scalar + 4, sizeof(double), cudaMemcpyHostToDevice, st));
+        if (kDF) to_df(b, b);
         pf_status s = solve(phiN, 1.0);
         if (iters) *iters = last_iters;
         if (relres) *relres = last_relres;
         if (s != PF_OK && s != PF_ERR_NOT_CONVERGED) return s;
-        launch_sum(g.ncell, p, rb, dsum, st);
-        launch_convert_out<double>(p, b, g.ncell, 0.0, dsum, 1.0 / g.ncell, st);
-        CK(cudaMemcpyAsync(x, b, bytes, cudaMemcpyDefault, st));
+        pressure_out(x);
         CK(cudaStreamSynchronize(st));
         return s;
     }

@@ -110,6 +110,19 @@ __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
     return quick_two_sum(p.hi, p.lo);
 }
 
+// a + b for double-floats (relative error about 2^-47)
+__device__ __forceinline__ f2 df_add(f2 a, f2 b) {
+    f2 s = two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ f2 df_neg(f2 a) { return f2{-a.hi, -a.lo}; }
+// a float64 value as a double-float (float64 operations: per-thread constants only)
+__device__ __forceinline__ f2 df_of(double v) {
+    const float h = __double2float_rn(v);
+    return f2{h, __double2float_rn(v - double(h))};
+}
+
 // Double-well term c psi'(phi) = c phi (1 - phi) (1 - 2 phi) for a float32 phi:
 // 1 - phi and 1 - 2 phi are formed exactly as double-floats and multiplied with
 // error-free products, so the float32 result is the float64 evaluation rounded
@@ -296,6 +309,50 @@ template <int K>
 __device__ __forceinline__ bool grid_reduce(double (&v)[K], const int (&mode)[K], RedBuf rb,
                                             double (&tot)[K]) {
     return grid_reduce_lin<K>(v, mode, rb, tot, blockIdx.x, gridDim.x);
+}
+
+// Scalars of the solve after an outer residual (totals: ||f||^2 when first,
+// ||f - A x||^2 twice): convergence, non-finite values, iteration cap, and
+// the inner tolerance of the next inner solve. Called by the last block.
+__device__ __forceinline__ void ir_finish(const double (&tot)[3], int first, CGScalars* sc) {
+    if (first) {
+        sc->ff = tot[0];
+        sc->iters = 0;
+        sc->outer = 0;
+        sc->capped = 0;
+        sc->done = 0;
+    }
+    const double ffv = sc->ff;
+    sc->rr = tot[1];
+    sc->rr0_in = tot[2];
+    sc->outer += 1;
+    sc->idone = 0;
+    if (!(tot[1] == tot[1])) {
+        sc->done = 1;
+        sc->status = 4;  // PF_ERR_NONFINITE
+    } else if (tot[1] <= sc->rtol2 * ffv) {
+        sc->done = 1;
+    } else if (sc->capped) {
+        sc->done = 1;
+        if (sc->status == 0) sc->status = 3;  // PF_ERR_NOT_CONVERGED
+    } else {
+        double e2 = sc->rtol2 * ffv / tot[1];
+        sc->eta2 = e2 > sc->eta2_min ? e2 : sc->eta2_min;
+    }
+}
+
+// One face term of a compensated double-float operator sum: adds
+// beta (x_c - x_q) with x_c = (ch, cl), x_q = (qh, ql) to the running sum S
+// and its error accumulator c (TwoSum of the hi parts, TwoProduct with beta,
+// TwoSum into S; every rounding error carried in c).
+__device__ __forceinline__ void df_face_term(float beta, float ch, float cl, float qh, float ql,
+                                             float& S, float& c) {
+    const f2 d = two_sum(ch, -qh);
+    const float t = __fadd_rn(d.lo, __fsub_rn(cl, ql));
+    const f2 pr = two_prod(beta, d.hi);
+    const f2 sm = two_sum(S, pr.hi);
+    S = sm.hi;
+    c = __fadd_rn(c, __fadd_rn(sm.lo, __fmaf_rn(beta, t, pr.lo)));
 }
 
 inline int red_grid(int n) {

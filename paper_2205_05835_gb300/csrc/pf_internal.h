@@ -154,6 +154,14 @@ bool dir3d_ok(const Dims& g);
 void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
                       const float* const* beta, int first, RedBuf rb, CGScalars* sc,
                       cudaStream_t s);
+// Float64-accurate outer residual r = sign (b - mean b) - A x of the mixed 3D
+// path (x, b double-floats: n hi parts then n lo parts; r float32), one thread
+// per column marching in z; also ||f||^2 (first) and ||r||^2 and the solve's
+// scalars.
+bool ir3d_ok(const Dims& g);
+void launch_ir_residual3d(const Dims& g, const float* x, const float* b, const float* const* beta,
+                          double sign, float* r, int first, RedBuf rb, CGScalars* sc,
+                          cudaStream_t s);
 // Restriction (mean of the children's residual) from a 3D float32 level with
 // face arrays and even sizes to the next coarser level.
 bool restrict3d_ok(const Dims& fine);
@@ -241,14 +249,12 @@ struct SolveIO {
     const T* phi;          // phase field defining rho
     const double* beta64[3];  // float64 face coefficients (T = double), else nullptr
     const float* beta32[3];   // float32 face coefficients (T = float), else nullptr
-    // optional (mixed path): beta32 widened to float64 and, per cell, the sum of
-    // its 2 DIM face coefficients; with them the float64 residual takes the
-    // expanded form x_c sum_q beta_q - sum_q beta_q x_q
-    const double* wide[3];
-    const double* diag;
-    const double* b;       // right-hand side (mean removed on the fly, times sign)
+    // right-hand side (mean removed on the fly, times sign) and solution (warm
+    // start): float64 arrays (T = double) or double-floats in the same 8 n
+    // bytes, n hi parts then n lo parts (T = float)
+    const double* b;
     double sign;
-    double* x;             // float64 solution (warm start)
+    double* x;
     T* r;                  // inner residual (= level-0 f of the V-cycle)
     T* z;                  // preconditioned residual (= level-0 x)
     T* p[2];               // search directions (double buffered)
@@ -261,7 +267,6 @@ void launch_beta0(const Dims& g, const Phys& ph, const T* phi, double* const* be
                   cudaStream_t s);
 template <int DIM>
 void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
-                     double* const* wide, double* diag,
                      cudaStream_t s);
 template <typename T, int DIM>
 void launch_mg_setup(const Dims& g0, const Phys& ph, const T* phi, MGHier<T>& H, cudaStream_t s);
@@ -287,6 +292,12 @@ template <typename T, int DIM>
 void launch_in_update(const Dims& g, const SolveIO<T, DIM>& io, int cur, int first, RedBuf rb,
                       CGScalars* sc, cudaStream_t s);
 void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s);
+// The mixed path keeps the pressure and the projection's right-hand side as
+// double-floats: n float hi parts followed by n float lo parts, in the 8 n
+// bytes of a float64 array of n entries.
+void launch_double_to_df(const double* src, float* hi, float* lo, int n, cudaStream_t s);
+void launch_df_to_double(const float* hi, const float* lo, double* dst, int n, cudaStream_t s);
+void launch_sub_mean(double* x, int n, const double* sum_ptr, double inv_n, cudaStream_t s);
 
 // ---- reverse mode (float64; pf_adjoint.cu) ----
 // Arrays of the transposed right-hand side of one stage (CDI + EB force).

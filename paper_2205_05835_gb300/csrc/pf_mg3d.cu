@@ -610,6 +610,135 @@ void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* 
 }  // namespace pf
 
 // ---------------------------------------------------------------------------
+// Outer residual of the mixed 3D path, r = sign (b - mean b) - A x, with x and
+// b double-floats (n hi parts, then n lo parts) and A formed from the float32
+// face coefficients by a compensated double-float sum on the float32 pipe
+// (df_face_term). One thread per column of a 32 x 8 tile marching in z: x of
+// the column at k-1, k, k+1 and the z-face coefficient above are carried in
+// registers, the in-plane neighbours come through L1.
+// ---------------------------------------------------------------------------
+namespace pf {
+namespace {
+
+struct IRArgs {
+    Dims g;
+    const float* xh;
+    const float* xl;
+    const float* bh;
+    const float* bl;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    float* r;
+    double sign;
+    int first;
+    int zc;
+    RedBuf rb;
+    CGScalars* sc;
+};
+
+__global__ void __launch_bounds__(256) k_ir_residual3d(IRArgs A) {
+    CGScalars* sc = A.sc;
+    if (!A.first && sc->done) return;
+    const Dims& g = A.g;
+    const int i = blockIdx.x * 32 + threadIdx.x % 32;
+    const int j = blockIdx.y * 8 + threadIdx.x / 32;
+    const int z0 = blockIdx.z * A.zc;
+    const int z1 = min(z0 + A.zc, g.nz);
+    float ff = 0.f, rr = 0.f;
+    if (i < g.nx && j < g.ny) {
+        const int sy = g.nx, sz = g.nx * g.ny;
+        const int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
+        const int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
+        const int col = j * sy + i;
+        const int o[4] = {im - i, ip - i, (jm - j) * sy, (jp - j) * sy};
+        const float* __restrict__ xh = A.xh;
+        const float* __restrict__ xl = A.xl;
+        const f2 mdf = df_neg(df_of(sc->mean_b));
+        const f2 ih2 = df_of(g.ih2);
+        const bool pos = A.sign > 0.0;
+        const int km1 = z0 == 0 ? g.nz - 1 : z0 - 1;
+        float mh = __ldg(xh + km1 * sz + col), ml = __ldg(xl + km1 * sz + col);
+        float ch = __ldg(xh + z0 * sz + col), cl = __ldg(xl + z0 * sz + col);
+        float bz_c = __ldg(A.bz + z0 * sz + col);
+        for (int k = z0; k < z1; ++k) {
+            const int idx = k * sz + col;
+            const int idxp = (k + 1 == g.nz ? 0 : k + 1) * sz + col;
+            // loads of the plane: in-plane neighbours, face coefficients, the
+            // column's next plane, the right-hand side
+            float nh[4], nl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                nh[q] = __ldg(xh + idx + o[q]);
+                nl[q] = __ldg(xl + idx + o[q]);
+            }
+            const float w[4] = {__ldg(A.bx + idx), __ldg(A.bx + idx + o[1]), __ldg(A.by + idx),
+                                __ldg(A.by + idx + o[3])};
+            const float ph_ = __ldg(xh + idxp), pl_ = __ldg(xl + idxp);
+            const float bz_n = __ldg(A.bz + idxp);
+            f2 f = df_add(f2{__ldg(A.bh + idx), __ldg(A.bl + idx)}, mdf);
+            if (!pos) f = df_neg(f);
+            float S = 0.f, c = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) df_face_term(w[q], ch, cl, nh[q], nl[q], S, c);
+            df_face_term(bz_c, ch, cl, mh, ml, S, c);
+            df_face_term(bz_n, ch, cl, ph_, pl_, S, c);
+            const f2 ax = f2_mul(two_sum(S, c), ih2);
+            const f2 rv = df_add(f, df_neg(ax));
+            const float rt = __fadd_rn(rv.hi, rv.lo);
+            A.r[idx] = rt;
+            if (A.first) {
+                const float ft = __fadd_rn(f.hi, f.lo);
+                ff += ft * ft;
+            }
+            rr += rt * rt;
+            mh = ch;
+            ml = cl;
+            ch = ph_;
+            cl = pl_;
+            bz_c = bz_n;
+        }
+    }
+    double v[3] = {double(ff), double(rr), double(rr)}, tot[3];
+    const int mode[3] = {0, 0, 0};
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (grid_reduce_lin<3>(v, mode, A.rb, tot, bid, nb) && threadIdx.x == 0)
+        ir_finish(tot, A.first, sc);
+}
+
+}  // namespace
+
+bool ir3d_ok(const Dims& g) {
+    return g.nz > 1 && 3LL * sweep3d_blocks(g) <= kRedPart;
+}
+
+void launch_ir_residual3d(const Dims& g, const float* x, const float* b, const float* const* beta,
+                          double sign, float* r, int first, RedBuf rb, CGScalars* sc,
+                          cudaStream_t s) {
+    IRArgs a;
+    a.g = g;
+    a.xh = x;
+    a.xl = x + g.ncell;
+    a.bh = b;
+    a.bl = b + g.ncell;
+    a.bx = beta[0];
+    a.by = beta[1];
+    a.bz = beta[2];
+    a.r = r;
+    a.sign = sign;
+    a.first = first;
+    a.rb = rb;
+    a.sc = sc;
+    const int zc = tiled_zc(g);
+    a.zc = zc;
+    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
+    k_ir_residual3d<<<grid, 256, 0, s>>>(a);
+}
+
+}  // namespace pf
+
+// ---------------------------------------------------------------------------
 // Restriction on 3D float32 levels with face arrays: f_C(I) = mean over the 8
 // children of the fine residual f - A x. One thread per coarse column (I, J)
 // marching in z; the 2 x 2 fine block of the planes k - 1, k, k + 1 and the

@@ -248,51 +248,30 @@ k_beta0(Dims g, Phys ph, const T* __restrict__ phi, double* __restrict__ b0,
 }
 
 // float32 face coefficients of the mixed path (the same beta_face32 as every
-// kernel that evaluates them from phi); optionally their float64 copies and
-// the per-cell sum of the 2 DIM coefficients of the cell. The plus-face
-// coefficient is recomputed here with the same operations (IEEE addition is
-// commutative), so the sum is over exactly the stored values; every float32
-// coefficient is exact in float64 and their sum is exact as long as the
-// coefficients span fewer than 2^26 in magnitude (density ratios far beyond
-// any in use), so the sum does not depend on the order of the additions.
+// kernel that evaluates them from phi)
 template <int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_beta0_32(Dims g, Phys ph, const float* __restrict__ phi, float* __restrict__ b0,
-           float* __restrict__ b1, float* __restrict__ b2, double* __restrict__ w0,
-           double* __restrict__ w1, double* __restrict__ w2, double* __restrict__ dg) {
+           float* __restrict__ b1, float* __restrict__ b2) {
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
         const float pc = __ldg(phi + idx);
-        const float m0 = beta_face32(pc, __ldg(phi + nb.m[0]), ph);
-        const float m1 = beta_face32(pc, __ldg(phi + nb.m[2]), ph);
-        const float m2 = DIM == 3 ? beta_face32(pc, __ldg(phi + nb.m[4]), ph) : 0.f;
-        b0[idx] = m0;
-        b1[idx] = m1;
-        if (DIM == 3) b2[idx] = m2;
-        if (dg != nullptr) {
-            w0[idx] = double(m0);
-            w1[idx] = double(m1);
-            if (DIM == 3) w2[idx] = double(m2);
-            double s = double(m0) + double(beta_face32(pc, __ldg(phi + nb.m[1]), ph));
-            s += double(m1) + double(beta_face32(pc, __ldg(phi + nb.m[3]), ph));
-            if (DIM == 3) s += double(m2) + double(beta_face32(pc, __ldg(phi + nb.m[5]), ph));
-            dg[idx] = s;
-        }
+        b0[idx] = beta_face32(pc, __ldg(phi + nb.m[0]), ph);
+        b1[idx] = beta_face32(pc, __ldg(phi + nb.m[2]), ph);
+        if (DIM == 3) b2[idx] = beta_face32(pc, __ldg(phi + nb.m[4]), ph);
     });
 }
 
 template <int DIM>
 void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
-                     double* const* wide, double* diag, cudaStream_t s) {
+                     cudaStream_t s) {
     k_beta0_32<DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
-        g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1],
-        diag ? wide[0] : nullptr, diag ? wide[1] : nullptr,
-        diag ? (DIM == 3 ? wide[2] : wide[1]) : nullptr, diag);
+        g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1]);
 }
 template void launch_beta0_32<2>(const Dims&, const Phys&, const float*, float* const*,
-                                 double* const*, double*, cudaStream_t);
+                                 cudaStream_t);
 template void launch_beta0_32<3>(const Dims&, const Phys&, const float*, float* const*,
-                                 double* const*, double*, cudaStream_t);
+                                 cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // single-CTA kernel for all levels >= first_coarse
@@ -537,6 +516,15 @@ __device__ __forceinline__ double apply_A64(const Dims& g, const Phys& ph,
 
 // r = f - A x with f = sign (b - mean b); r stored in T for the inner solve.
 // first: also ||f||^2 and the solve's counters.
+// Float64 path: x, b float64. Mixed path: x and b are double-floats (hi plane,
+// lo plane) and the residual is formed with error-free transformations on the
+// float32 pipe (GB300's float64 pipe is narrow): each x_c - x_q as an exact
+// TwoSum of the hi parts plus the lo difference, each product with the float32
+// face coefficient as an exact TwoProduct, the six products summed with
+// TwoSum and every rounding error carried in a second float (a compensated
+// dot product, as accurate as evaluation in twice the working precision). Its
+// rounding floor is about 2^-48 |x| |sum beta| per cell, i.e. a relative
+// residual near 1e-16 N^2 for a smooth solution on an N-cell axis.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_ir_residual(Dims g, Phys ph, SolveIO<T, DIM> io, int first, RedBuf rb, CGScalars* sc) {
@@ -544,93 +532,98 @@ k_ir_residual(Dims g, Phys ph, SolveIO<T, DIM> io, int first, RedBuf rb, CGScala
     const double mb = sc->mean_b;
     const bool pos = io.sign > 0.0;
     // norms accumulate the rounded values per thread in T (a stopping test
-    // needs a few digits); the residual itself is formed in float64
+    // needs a few digits); the residual itself is formed to float64 accuracy
     T ff = T(0), rr = T(0);
-    for_cells(g, [&](int i, int j, int k, int idx) {
-        const double f = pos ? io.b[idx] - mb : mb - io.b[idx];
-        double rv;
-        if (io.diag != nullptr) {
-            // the same operator as x_c sum_q beta_q - sum_q beta_q x_q (the sum
-            // is exact): one multiply-add per face instead of a subtraction and
-            // a conversion and a multiply-add. Its cancellation leaves a rounding
-            // error of a few units in the last place of |x| sum_q beta_q,
-            // relative to ||f|| at most about 2.5e-17 N^2 (a smooth solution);
-            // the context selects this form only for tolerances well above that.
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const int n = g.ncell;
+        const float* __restrict__ xh = reinterpret_cast<const float*>(io.x);
+        const float* __restrict__ xl = xh + n;
+        const float* __restrict__ bh = reinterpret_cast<const float*>(io.b);
+        const float* __restrict__ bl = bh + n;
+        const f2 mdf = df_neg(df_of(mb));
+        const f2 ih2 = df_of(g.ih2);
+        for_cells(g, [&](int i, int j, int k, int idx) {
+            f2 f = df_add(f2{bh[idx], bl[idx]}, mdf);
+            if (!pos) f = df_neg(f);
             const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
-            const double* __restrict__ x = io.x;
-            double s = io.wide[0][idx] * x[nb.m[0]];
-            s = fma(io.wide[0][nb.m[1]], x[nb.m[1]], s);
-            s = fma(io.wide[1][idx], x[nb.m[2]], s);
-            s = fma(io.wide[1][nb.m[3]], x[nb.m[3]], s);
-            if (DIM == 3) {
-                s = fma(io.wide[2][idx], x[nb.m[4]], s);
-                s = fma(io.wide[2][nb.m[5]], x[nb.m[5]], s);
+            const float xch = xh[idx], xcl = xl[idx];
+            const float pc = io.beta32[0] != nullptr ? 0.f : float(__ldg(io.phi + idx));
+            float S = 0.f, c = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2 * DIM; ++q) {
+                const int m = nb.m[q];
+                // face q of the cell: the minus face is stored at the cell, the
+                // plus face at the neighbour
+                float beta;
+                if (io.beta32[0] != nullptr)
+                    beta = __ldg(io.beta32[q >> 1] + ((q & 1) ? m : idx));
+                else
+                    beta = beta_face32(pc, float(__ldg(io.phi + m)), ph);
+                df_face_term(beta, xch, xcl, xh[m], xl[m], S, c);
             }
-            rv = fma(-g.ih2, fma(x[idx], io.diag[idx], -s), f);
-        } else {
-            rv = f - apply_A64<T, DIM>(g, ph, io, io.x, i, j, k, idx);
-        }
-        const T rt = T(rv);
-        io.r[idx] = rt;
-        if (first) {
-            const T ft = T(f);
-            ff += ft * ft;
-        }
-        rr += rt * rt;
-    });
+            const f2 ax = f2_mul(two_sum(S, c), ih2);
+            const f2 r = df_add(f, df_neg(ax));
+            const float rt = __fadd_rn(r.hi, r.lo);
+            io.r[idx] = rt;
+            if (first) {
+                const float ft = __fadd_rn(f.hi, f.lo);
+                ff += ft * ft;
+            }
+            rr += rt * rt;
+        });
+    } else {
+        for_cells(g, [&](int i, int j, int k, int idx) {
+            const double f = pos ? io.b[idx] - mb : mb - io.b[idx];
+            const double rv = f - apply_A64<T, DIM>(g, ph, io, io.x, i, j, k, idx);
+            const T rt = T(rv);
+            io.r[idx] = rt;
+            if (first) {
+                const T ft = T(f);
+                ff += ft * ft;
+            }
+            rr += rt * rt;
+        });
+    }
     double v[3] = {double(ff), double(rr), double(rr)}, tot[3];
     const int mode[3] = {0, 0, 0};
-    if (grid_reduce<3>(v, mode, rb, tot) && threadIdx.x == 0) {
-        if (first) {
-            sc->ff = tot[0];
-            sc->iters = 0;
-            sc->outer = 0;
-            sc->capped = 0;
-            sc->done = 0;
-        }
-        const double ffv = sc->ff;
-        sc->rr = tot[1];
-        sc->rr0_in = tot[2];
-        sc->outer += 1;
-        sc->idone = 0;
-        if (!(tot[1] == tot[1])) {
-            sc->done = 1;
-            sc->status = 4;  // PF_ERR_NONFINITE
-        } else if (tot[1] <= sc->rtol2 * ffv) {
-            sc->done = 1;
-        } else if (sc->capped) {
-            sc->done = 1;
-            if (sc->status == 0) sc->status = 3;  // PF_ERR_NOT_CONVERGED
-        } else {
-            double e2 = sc->rtol2 * ffv / tot[1];
-            sc->eta2 = e2 > sc->eta2_min ? e2 : sc->eta2_min;
-        }
-    }
+    if (grid_reduce<3>(v, mode, rb, tot) && threadIdx.x == 0) ir_finish(tot, first, sc);
 }
 
-// x += e
+// x += e (mixed path: x a double-float, hi plane and lo plane)
+__device__ __forceinline__ void df_acc(float& h, float& l, float e) {
+    const f2 s = two_sum(h, e);
+    const f2 r = two_sum(s.hi, __fadd_rn(s.lo, l));
+    h = r.hi;
+    l = r.lo;
+}
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_ir_addcorr(Dims g, SolveIO<T, DIM> io, const CGScalars* sc) {
     if (sc->done) return;
     if constexpr (sizeof(T) == sizeof(float)) {
+        float* __restrict__ xh = reinterpret_cast<float*>(io.x);
+        float* __restrict__ xl = xh + g.ncell;
+        const int stride = gridDim.x * blockDim.x;
         if ((g.ncell & 3) == 0) {
             const int n4 = g.ncell >> 2;
             const float4* __restrict__ e4 = reinterpret_cast<const float4*>(io.e);
-            double2* __restrict__ x2 = reinterpret_cast<double2*>(io.x);
-            const int stride = gridDim.x * blockDim.x;
+            float4* __restrict__ h4 = reinterpret_cast<float4*>(xh);
+            float4* __restrict__ l4 = reinterpret_cast<float4*>(xl);
             for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
                 const float4 ev = e4[t];
-                double2 a = x2[2 * t], b = x2[2 * t + 1];
-                a.x += double(ev.x);
-                a.y += double(ev.y);
-                b.x += double(ev.z);
-                b.y += double(ev.w);
-                x2[2 * t] = a;
-                x2[2 * t + 1] = b;
+                float4 h = h4[t], l = l4[t];
+                df_acc(h.x, l.x, ev.x);
+                df_acc(h.y, l.y, ev.y);
+                df_acc(h.z, l.z, ev.z);
+                df_acc(h.w, l.w, ev.w);
+                h4[t] = h;
+                l4[t] = l;
             }
             return;
         }
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += stride)
+            df_acc(xh[t], xl[t], io.e[t]);
+        return;
     }
     for_cells(g, [&](int, int, int, int idx) { io.x[idx] += double(io.e[idx]); });
 }
@@ -778,6 +771,14 @@ k_in_update(Dims g, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGScalars
 template <typename T, int DIM>
 void launch_ir_residual(const Dims& g, const Phys& ph, const SolveIO<T, DIM>& io, int first,
                         RedBuf rb, CGScalars* sc, cudaStream_t s) {
+    if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        if (io.beta32[0] != nullptr && ir3d_ok(g)) {
+            launch_ir_residual3d(g, reinterpret_cast<const float*>(io.x),
+                                 reinterpret_cast<const float*>(io.b), io.beta32, io.sign,
+                                 reinterpret_cast<float*>(io.r), first, rb, sc, s);
+            return;
+        }
+    }
     k_ir_residual<T, DIM><<<row_grid(g, kThreads, kRedBlocks), kThreads, 0, s>>>(g, ph, io, first,
                                                                                   rb, sc);
 }

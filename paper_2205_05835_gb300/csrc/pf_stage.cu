@@ -557,7 +557,9 @@ void launch_gamma(const Dims& g, const T* const* u, double gamma_fixed, double g
 }
 
 // ---------------------------------------------------------------------------
-// b = D u* / tau (float64) and its sum (the mean is removed by the solver)
+// b = D u* / tau and its sum (the mean is removed by the solver). Float64
+// path: b float64. Mixed path: b a double-float (hi plane, then lo plane in
+// the same 8 n bytes), formed without the float64 pipe.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
@@ -565,16 +567,20 @@ k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T
              double inv_tau, double* __restrict__ b, RedBuf rb, CGScalars* sc) {
     double s = 0.0;
     const double inv_h = g.ih;
+    f2 acc{0.f, 0.f};
+    const f2 scale = sizeof(T) == sizeof(float) ? df_of(inv_h * inv_tau) : f2{0.f, 0.f};
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
-        double dv;
         if (sizeof(T) == sizeof(double)) {
-            dv = (double(u0[nb.m[1]]) - double(u0[idx])) * inv_h;
+            double dv = (double(u0[nb.m[1]]) - double(u0[idx])) * inv_h;
             dv += (double(u1[nb.m[3]]) - double(u1[idx])) * inv_h;
             if (DIM == 3) dv += (double(u2[nb.m[5]]) - double(u2[idx])) * inv_h;
+            dv *= inv_tau;
+            b[idx] = dv;
+            s += dv;
         } else {
             // float32 velocities: exact differences (TwoSum) summed as a
-            // double-float, converted once to float64
+            // double-float and scaled by 1 / (h tau) as a double-float
             const float* uf0 = reinterpret_cast<const float*>(u0);
             const float* uf1 = reinterpret_cast<const float*>(u1);
             const float* uf2 = reinterpret_cast<const float*>(u2);
@@ -588,12 +594,14 @@ k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T
                 t2.lo = __fadd_rn(t2.lo, __fadd_rn(t.lo, c1.lo));
                 t = t2;
             }
-            dv = (double(t.hi) + double(t.lo)) * inv_h;
+            const f2 r = f2_mul(t, scale);
+            float* bf = reinterpret_cast<float*>(b);
+            bf[idx] = r.hi;
+            bf[idx + g.ncell] = r.lo;
+            acc = df_add(acc, r);
         }
-        dv *= inv_tau;
-        b[idx] = dv;
-        s += dv;
     });
+    if (sizeof(T) == sizeof(float)) s = double(acc.hi) + double(acc.lo);
     double v[1] = {s}, tot[1];
     const int mode[1] = {0};
     if (grid_reduce<1>(v, mode, rb, tot) && threadIdx.x == 0) sc->mean_b = tot[0] / g.ncell;
@@ -627,7 +635,7 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
     const float tau_h = float(tau * g.ih);
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
-        const double pp = p[idx];
+        const double pp = b0 != nullptr ? p[idx] : 0.0;
         const T* sv[3] = {s0, s1, s2};
         T* ov[3] = {o0, o1, o2};
         const double* bv[3] = {b0, b1, b2};
@@ -641,10 +649,14 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
                 ov[d][idx] = T(double(sv[d][idx]) - tau * bv[d][idx] * gp);
             } else {
                 // float32 path: same beta as the pressure operator; the pressure
-                // difference is formed in float64, scaled and applied in float32
+                // is a double-float (hi plane, lo plane), its difference formed
+                // from both parts, scaled and applied in float32
                 const float beta = f0 != nullptr ? __ldg(fv[d] + idx)
                                                  : beta_face32(float(phi[idx]), float(phi[m]), ph);
-                const float gp = float(pp - p[m]) * tau_h;
+                const float* ph_ = reinterpret_cast<const float*>(p);
+                const float* pl_ = ph_ + g.ncell;
+                const float gp =
+                    __fadd_rn(__fsub_rn(ph_[idx], ph_[m]), __fsub_rn(pl_[idx], pl_[m])) * tau_h;
                 ov[d][idx] = T(float(sv[d][idx]) - beta * gp);
             }
         }
@@ -706,7 +718,14 @@ k_diag(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ u0,
         mass += pc;
         pmin = fmin(pmin, pc);
         pmax = fmax(pmax, pc);
-        double pp = p[idx];
+        double pp;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            // mixed path: the pressure is a double-float (hi plane, lo plane)
+            const float* pf = reinterpret_cast<const float*>(p);
+            pp = double(pf[idx]) + double(pf[idx + g.ncell]);
+        } else {
+            pp = p[idx];
+        }
         psum += pp;
         if (pc >= 0.999) { pin += pp; nin += 1.0; }
         if (pc <= 0.001) { pout += pp; nout += 1.0; }
@@ -738,6 +757,39 @@ void launch_diagnostics(const Dims& g, const Phys& ph, const T* phi, const T* co
                         const double* p, RedBuf rb, DiagOut* out, cudaStream_t s) {
     k_diag<T, DIM><<<row_grid(g, kThreads, kRedBlocks), kThreads, 0, s>>>(g, ph, phi, u[0], u[1],
                                                            DIM == 3 ? u[2] : u[0], p, rb, out);
+}
+
+// ---------------------------------------------------------------------------
+// double-float planes <-> float64 (API transfers of the mixed path's pressure
+// and right-hand side)
+// ---------------------------------------------------------------------------
+__global__ void k_double_to_df(const double* __restrict__ src, float* __restrict__ hi,
+                               float* __restrict__ lo, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const f2 v = df_of(src[i]);
+        hi[i] = v.hi;
+        lo[i] = v.lo;
+    }
+}
+__global__ void k_df_to_double(const float* __restrict__ hi, const float* __restrict__ lo,
+                               double* __restrict__ dst, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = double(hi[i]) + double(lo[i]);
+}
+__global__ void k_sub_mean(double* x, int n, const double* sum_ptr, double inv_n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double m = (*sum_ptr) * inv_n;
+    if (i < n) x[i] -= m;
+}
+void launch_double_to_df(const double* src, float* hi, float* lo, int n, cudaStream_t s) {
+    k_double_to_df<<<lin_grid(n), kThreads, 0, s>>>(src, hi, lo, n);
+}
+void launch_df_to_double(const float* hi, const float* lo, double* dst, int n, cudaStream_t s) {
+    k_df_to_double<<<lin_grid(n), kThreads, 0, s>>>(hi, lo, dst, n);
+}
+void launch_sub_mean(double* x, int n, const double* sum_ptr, double inv_n, cudaStream_t s) {
+    k_sub_mean<<<lin_grid(n), kThreads, 0, s>>>(x, n, sum_ptr, inv_n);
 }
 
 // ---------------------------------------------------------------------------

@@ -104,12 +104,14 @@ __global__ void __launch_bounds__(ZT) k_divergence3d(DivArgs A) {
     const Col c = column(g);
     const int sz = g.nx * g.ny;
     const int z0 = blockIdx.z * A.zc, z1 = min(z0 + A.zc, g.nz);
-    double s = 0.0;
+    f2 acc{0.f, 0.f};
     if (c.own) {
         const float* __restrict__ u0 = A.u0;
         const float* __restrict__ u1 = A.u1;
         const float* __restrict__ u2 = A.u2;
-        double* __restrict__ b = A.b;
+        float* __restrict__ bh = reinterpret_cast<float*>(A.b);
+        float* __restrict__ bl = bh + g.ncell;
+        const f2 scale = df_of(A.scale);
         float wc = __ldg(u2 + z0 * sz + c.col);
 #pragma unroll 2
         for (int k = z0; k < z1; ++k) {
@@ -123,13 +125,15 @@ __global__ void __launch_bounds__(ZT) k_divergence3d(DivArgs A) {
             const f2 c1 = two_sum(wp, -wc);
             f2 t2 = two_sum(t.hi, c1.hi);
             t2.lo = __fadd_rn(t2.lo, __fadd_rn(t.lo, c1.lo));
-            const double dv = (double(t2.hi) + double(t2.lo)) * A.scale;
-            b[idx] = dv;
-            s += dv;
+            // b as a double-float (hi plane, lo plane), scaled by 1 / (h tau)
+            const f2 dv = f2_mul(t2, scale);
+            bh[idx] = dv.hi;
+            bl[idx] = dv.lo;
+            acc = df_add(acc, dv);
             wc = wp;
         }
     }
-    double v[1] = {s}, tot[1];
+    double v[1] = {double(acc.hi) + double(acc.lo)}, tot[1];
     const int mode[1] = {0};
     const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const int nb = gridDim.x * gridDim.y * gridDim.z;
@@ -159,21 +163,26 @@ __global__ void __launch_bounds__(ZT) k_correct3d(CorrArgs A) {
     if (!c.own) return;
     const int sz = g.nx * g.ny;
     const int z0 = blockIdx.z * A.zc, z1 = min(z0 + A.zc, g.nz);
-    const double* __restrict__ p = A.p;
+    // the pressure is a double-float: hi plane, then lo plane
+    const float* __restrict__ ph = reinterpret_cast<const float*>(A.p);
+    const float* __restrict__ pl = ph + g.ncell;
     const float tau_h = A.tau_h;
-    double pm = p[(z0 == 0 ? g.nz - 1 : z0 - 1) * sz + c.col];
+    const int i0 = (z0 == 0 ? g.nz - 1 : z0 - 1) * sz + c.col;
+    float pmh = ph[i0], pml = pl[i0];
 #pragma unroll 2
     for (int k = z0; k < z1; ++k) {
         const int idx = k * sz + c.col;
-        const double pc = p[idx];
-        // the pressure difference in float64, scaled and applied in float32
-        const float gx = float(pc - p[idx + c.ox_m]) * tau_h;
-        const float gy = float(pc - p[idx + c.oy_m]) * tau_h;
-        const float gz = float(pc - pm) * tau_h;
+        const float pch = ph[idx], pcl = pl[idx];
+        // the pressure difference from both parts, scaled and applied in float32
+        const int ix = idx + c.ox_m, iy = idx + c.oy_m;
+        const float gx = __fadd_rn(__fsub_rn(pch, ph[ix]), __fsub_rn(pcl, pl[ix])) * tau_h;
+        const float gy = __fadd_rn(__fsub_rn(pch, ph[iy]), __fsub_rn(pcl, pl[iy])) * tau_h;
+        const float gz = __fadd_rn(__fsub_rn(pch, pmh), __fsub_rn(pcl, pml)) * tau_h;
         A.o0[idx] = __ldg(A.s0 + idx) - __ldg(A.f0 + idx) * gx;
         A.o1[idx] = __ldg(A.s1 + idx) - __ldg(A.f1 + idx) * gy;
         A.o2[idx] = __ldg(A.s2 + idx) - __ldg(A.f2 + idx) * gz;
-        pm = pc;
+        pmh = pch;
+        pml = pcl;
     }
 }
 

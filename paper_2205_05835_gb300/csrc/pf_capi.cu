@@ -198,6 +198,9 @@ struct ImplT final : Impl {
     };
     Tape* tape = nullptr;
     double* xsolve = nullptr;
+    // Pressure of the first projection of an RK4 step (its solve target); the
+    // state's pressure p holds the other three in turn (see one_step).
+    double* pw = nullptr;
     int last_iters = 0, max_iters = 0;
     double last_relres = 0.0, last_gamma = 0.0;
     int host_status = 0;
@@ -307,6 +310,7 @@ struct ImplT final : Impl {
         aux = cv.take<T>(2 * n);
         p = cv.take<double>(n);
         b = cv.take<double>(n);
+        pw = prm.scheme == PF_FE ? nullptr : cv.take<double>(n);
         rT = cv.take<T>(n);
         z = cv.take<T>(n);
         pd[0] = cv.take<T>(n);
@@ -481,7 +485,8 @@ struct ImplT final : Impl {
         if (s != PF_OK) return s;
         prof.begin(KC_CORRECT);
         launch_correct<T, DIM>(g, ph, phi, sizeof(T) == sizeof(double) ? beta64 : nullptr,
-                               beta32[0] ? beta32 : nullptr, uin_c, p, tau, uout, st);
+                               beta32[0] ? beta32 : nullptr, uin_c, xsolve ? xsolve : p, tau,
+                               uout, st);
         prof.end();
         return PF_OK;
     }
@@ -660,17 +665,36 @@ struct ImplT final : Impl {
             prof.begin(KC_STAGE);
             launch_stage<T, DIM>(g, ph, io, s, 0, wdt, cdt, 0, st);
             prof.end();
+            // Initial guesses of the four pressure solves. Projection s carries
+            // the pressure of k_s, whose time level is t^n, t^n + dt/2,
+            // t^n + dt/2 and (Simpson's mean of the four) t^n + dt/2 + O(dt^2);
+            // the state's pressure p is the last projection of the previous
+            // step (t^n - dt/2). So projection 0 starts from p, projection 1
+            // from the linear extrapolation 2 p_0 - p (second order in dt),
+            // projections 2 and 3 from their predecessor. Only the state and
+            // this step enter the guess, so a restart from a saved state
+            // reproduces the run bit for bit.
+            if (s == 0) {
+                cudaMemcpyAsync(pw, p, (size_t)g.ncell * sizeof(double), cudaMemcpyDeviceToDevice,
+                                st);
+                xsolve = pw;
+            } else if (s == 1) {
+                launch_extrapolate(g.ncell, sizeof(T) == sizeof(float), pw, p, p, st);
+            }
+            double* xs = xsolve ? xsolve : p;
             pf_status ps = do_project(phout[s], uStar, cdt, s < 3 ? uS : uN);
+            xsolve = nullptr;
             if (ps != PF_OK) return ps;
             if (tape) {
                 tape_copy(tape->phi[s + 1], phout[s]);
                 if (s < 3)
                     for (int d = 0; d < DIM; ++d) tape_copy(tape->u[s + 1][d], uS[d]);
-                tape_copy(tape->p[s], p);
+                tape_copy(tape->p[s], xs);
             }
         }
         return PF_OK;
     }
+
 
     template <typename Q>
     void tape_copy(Q* dst, const Q* src) {

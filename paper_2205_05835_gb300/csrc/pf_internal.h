@@ -298,6 +298,9 @@ void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s);
 void launch_double_to_df(const double* src, float* hi, float* lo, int n, cudaStream_t s);
 void launch_df_to_double(const float* hi, const float* lo, double* dst, int n, cudaStream_t s);
 void launch_sub_mean(double* x, int n, const double* sum_ptr, double inv_n, cudaStream_t s);
+// out = 2 a - b elementwise (float64, or double-float planes when df); out may be b
+void launch_extrapolate(int n, bool df, const double* a, const double* b, double* out,
+                        cudaStream_t s);
 
 // ---- reverse mode (float64; pf_adjoint.cu) ----
 // Arrays of the transposed right-hand side of one stage (CDI + EB force).

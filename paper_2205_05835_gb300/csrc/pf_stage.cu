@@ -782,6 +782,25 @@ __global__ void k_sub_mean(double* x, int n, const double* sum_ptr, double inv_n
     const double m = (*sum_ptr) * inv_n;
     if (i < n) x[i] -= m;
 }
+// out = 2 a - b (float64 arrays, or double-float planes when df); out may be b
+__global__ void k_extrapolate(int n, int df, const double* a, const double* b, double* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (df) {
+        const float* ah = reinterpret_cast<const float*>(a);
+        const float* bh = reinterpret_cast<const float*>(b);
+        float* oh = reinterpret_cast<float*>(out);
+        const f2 v = df_add(f2{2.f * ah[i], 2.f * ah[i + n]}, f2{-bh[i], -bh[i + n]});
+        oh[i] = v.hi;
+        oh[i + n] = v.lo;
+    } else {
+        out[i] = 2.0 * a[i] - b[i];
+    }
+}
+void launch_extrapolate(int n, bool df, const double* a, const double* b, double* out,
+                        cudaStream_t s) {
+    k_extrapolate<<<lin_grid(n), kThreads, 0, s>>>(n, df ? 1 : 0, a, b, out);
+}
 void launch_double_to_df(const double* src, float* hi, float* lo, int n, cudaStream_t s) {
     k_double_to_df<<<lin_grid(n), kThreads, 0, s>>>(src, hi, lo, n);
 }

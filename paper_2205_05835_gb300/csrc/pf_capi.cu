@@ -176,6 +176,7 @@ struct ImplT final : Impl {
     double *p, *b;
     double* beta64[3];   // float64 face coefficients (float64 path only)
     float* beta32[3] = {nullptr, nullptr, nullptr};  // float32 face coefficients (mixed path)
+    float* rho0 = nullptr;                            // float32 cell densities (3D mixed path)
     T *rT, *z, *pd[2], *qT, *eT;
     MGHier<T> H;
     RedBuf rb;
@@ -321,6 +322,10 @@ struct ImplT final : Impl {
             beta64[d] = (sizeof(T) == sizeof(double) && d < DIM) ? cv.take<double>(n) : nullptr;
         for (int d = 0; d < 3; ++d)
             beta32[d] = (sizeof(T) == sizeof(float) && d < DIM) ? cv.take<float>(n) : nullptr;
+        if (DIM == 3 && sizeof(T) == sizeof(float)) {
+            rho0 = cv.take<float>(n);
+            H.rho0 = rho0;
+        }
         H.lev[0].x = z;
         H.lev[0].f = rT;
         for (int d = 0; d < 3; ++d)
@@ -531,7 +536,7 @@ struct ImplT final : Impl {
             prof.end();
         } else if (beta32[0] != nullptr) {
             prof.begin(KC_BETA0);
-            launch_beta0_32<DIM>(g, ph, reinterpret_cast<const float*>(phi), beta32, st);
+            launch_beta0_32<DIM>(g, ph, reinterpret_cast<const float*>(phi), beta32, rho0, st);
             prof.end();
         }
         prof.begin(KC_COARSEN);

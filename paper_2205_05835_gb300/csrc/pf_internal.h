@@ -124,6 +124,8 @@ struct MGLevel {
 
 template <typename T>
 struct MGHier {
+    const float* rho0 = nullptr;   // float32 cell densities of level 0 (3D mixed path), formed
+                                   // once per solve; the finest sweep reads them instead of phi
     int nlev;
     int first_coarse;   // levels >= first_coarse are handled by one single-CTA kernel
     int pre, post;
@@ -175,9 +177,10 @@ void launch_divergence3d(const Dims& g, const float* const* u, double inv_tau, d
                          RedBuf rb, CGScalars* sc, cudaStream_t s);
 void launch_correct3d(const Dims& g, const float* const* beta32, const float* const* ustar,
                       const double* p, double tau, float* const* uout, cudaStream_t s);
-// phi != nullptr: finest level, smoother weights from rho(phi); else the
-// level's face coefficient arrays
-void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
+// phi != nullptr: finest level, smoother weights from rho(phi) (rho_ready: the
+// array already holds rho); else the level's face coefficient arrays
+void launch_sweep3d(const MGLevel<float>& L, const float* phi, int rho_ready, const Phys& ph,
+                    const float* xin,
                     float* xout, const SweepDots* dots, int first_color, const CGScalars* sc,
                     cudaStream_t s);
 
@@ -267,7 +270,7 @@ void launch_beta0(const Dims& g, const Phys& ph, const T* phi, double* const* be
                   cudaStream_t s);
 template <int DIM>
 void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
-                     cudaStream_t s);
+                     float* rho, cudaStream_t s);
 template <typename T, int DIM>
 void launch_mg_setup(const Dims& g0, const Phys& ph, const T* phi, MGHier<T>& H, cudaStream_t s);
 // Runs one V-cycle; returns the level-0 buffer that holds the result. With

@@ -82,6 +82,7 @@ struct SweepArgs {
     const float* by;
     const float* bz;
     Phys ph;
+    int rho_ready;        // phi already holds rho32(phi)
     float fs;             // f scale: h^2 / 2 (from phi) or h^2 (face arrays)
     int first_color;
     int zc;
@@ -184,7 +185,7 @@ __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* 
     // rho(phi) in place for this thread's own chunks of the plane at ring
     // offset o (after their copies landed)
     auto transform = [&](int o, bool used) {
-        if (FROM_PHI && used) {
+        if (FROM_PHI && used && !A.rho_ready) {
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 if (!has[c]) continue;
@@ -406,11 +407,12 @@ bool sweep3d_ok(const Dims& g) {
            g.ny >= 4 && g.nz >= 4;
 }
 
-void launch_sweep3d(const MGLevel<float>& L, const float* phi, const Phys& ph, const float* xin,
-                    float* xout, const SweepDots* dots, int first_color, const CGScalars* sc,
-                    cudaStream_t s) {
+void launch_sweep3d(const MGLevel<float>& L, const float* phi, int rho_ready, const Phys& ph,
+                    const float* xin, float* xout, const SweepDots* dots, int first_color,
+                    const CGScalars* sc, cudaStream_t s) {
     SweepArgs a;
     a.g = L.g;
+    a.rho_ready = rho_ready;
     a.xin = xin;
     a.f = L.f;
     a.xout = xout;

@@ -248,14 +248,16 @@ k_beta0(Dims g, Phys ph, const T* __restrict__ phi, double* __restrict__ b0,
 }
 
 // float32 face coefficients of the mixed path (the same beta_face32 as every
-// kernel that evaluates them from phi)
+// kernel that evaluates them from phi) and, optionally, the cell densities
+// rho32(phi) that the finest smoother reads
 template <int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_beta0_32(Dims g, Phys ph, const float* __restrict__ phi, float* __restrict__ b0,
-           float* __restrict__ b1, float* __restrict__ b2) {
+           float* __restrict__ b1, float* __restrict__ b2, float* __restrict__ rho) {
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
         const float pc = __ldg(phi + idx);
+        if (rho) rho[idx] = rho32(pc, ph);
         b0[idx] = beta_face32(pc, __ldg(phi + nb.m[0]), ph);
         b1[idx] = beta_face32(pc, __ldg(phi + nb.m[2]), ph);
         if (DIM == 3) b2[idx] = beta_face32(pc, __ldg(phi + nb.m[4]), ph);
@@ -264,13 +266,13 @@ k_beta0_32(Dims g, Phys ph, const float* __restrict__ phi, float* __restrict__ b
 
 template <int DIM>
 void launch_beta0_32(const Dims& g, const Phys& ph, const float* phi, float* const* beta,
-                     cudaStream_t s) {
+                     float* rho, cudaStream_t s) {
     k_beta0_32<DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
-        g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1]);
+        g, ph, phi, beta[0], beta[1], DIM == 3 ? beta[2] : beta[1], rho);
 }
-template void launch_beta0_32<2>(const Dims&, const Phys&, const float*, float* const*,
+template void launch_beta0_32<2>(const Dims&, const Phys&, const float*, float* const*, float*,
                                  cudaStream_t);
-template void launch_beta0_32<3>(const Dims&, const Phys&, const float*, float* const*,
+template void launch_beta0_32<3>(const Dims&, const Phys&, const float*, float* const*, float*,
                                  cudaStream_t);
 
 // ---------------------------------------------------------------------------
@@ -383,6 +385,9 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                  cudaStream_t s, Prof* pr, const SweepDots* dots, bool* dots_done) {
     if (dots_done) *dots_done = false;
     const int l0 = H.first_coarse;
+    // finest tiled sweep: the precomputed cell densities when present, else phi
+    const float* phi0 = H.rho0 != nullptr ? H.rho0 : reinterpret_cast<const float*>(phi);
+    const int rho_ready = H.rho0 != nullptr ? 1 : 0;
     T* fin[kMaxLevels];   // buffer holding each level's result
     for (int l = l0; l < H.nlev; ++l) fin[l] = H.lev[l].x;
     auto gs = [&](const MGLevel<T>& L, int lvl, int color, int zero) {
@@ -402,8 +407,8 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                 T* oth = L.x2;
                 for (int p = 0; p < H.pre; ++p) {
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
-                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
-                                   l == 0 ? reinterpret_cast<const float*>(phi) : nullptr, ph,
+                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L), l == 0 ? phi0 : nullptr,
+                                   rho_ready, ph,
                                    p == 0 ? nullptr : reinterpret_cast<const float*>(cur),
                                    reinterpret_cast<float*>(p == 0 ? cur : oth), nullptr, 0, sc, s);
                     pr->end();
@@ -456,8 +461,8 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                     const bool fuse = dots && l == 0 && p == H.post - 1 &&
                                       2 * sweep3d_blocks(L.g) <= kRedPart;
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
-                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
-                                   l == 0 ? reinterpret_cast<const float*>(phi) : nullptr, ph,
+                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L), l == 0 ? phi0 : nullptr,
+                                   rho_ready, ph,
                                    reinterpret_cast<const float*>(cur), reinterpret_cast<float*>(oth),
                                    fuse ? dots : nullptr, 1, sc, s);
                     pr->end();

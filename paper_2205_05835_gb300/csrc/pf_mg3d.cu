@@ -113,7 +113,6 @@ __device__ __forceinline__ int ring(int o, int d) {
     o += o < 0 ? R * P : 0;
     return o >= R * P ? o - R * P : o;
 }
-
 template <bool FROM_PHI, int V>
 __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* smem_raw) {
     using G = Geo<V>;
@@ -663,28 +662,38 @@ __global__ void __launch_bounds__(256) k_ir_residual3d(IRArgs A) {
         float mh = __ldg(xh + km1 * sz + col), ml = __ldg(xl + km1 * sz + col);
         float ch = __ldg(xh + z0 * sz + col), cl = __ldg(xl + z0 * sz + col);
         float bz_c = __ldg(A.bz + z0 * sz + col);
-        for (int k = z0; k < z1; ++k) {
+        // the loads of plane k: in-plane neighbours, face coefficients, the
+        // column's next plane and the right-hand side
+        struct Ld {
+            float nh[4], nl[4], w[4], ph, pl, bzn, bh, bl;
+        };
+        auto load = [&](int k, Ld& L) {
             const int idx = k * sz + col;
             const int idxp = (k + 1 == g.nz ? 0 : k + 1) * sz + col;
-            // loads of the plane: in-plane neighbours, face coefficients, the
-            // column's next plane, the right-hand side
-            float nh[4], nl[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                nh[q] = __ldg(xh + idx + o[q]);
-                nl[q] = __ldg(xl + idx + o[q]);
+                L.nh[q] = __ldg(xh + idx + o[q]);
+                L.nl[q] = __ldg(xl + idx + o[q]);
             }
-            const float w[4] = {__ldg(A.bx + idx), __ldg(A.bx + idx + o[1]), __ldg(A.by + idx),
-                                __ldg(A.by + idx + o[3])};
-            const float ph_ = __ldg(xh + idxp), pl_ = __ldg(xl + idxp);
-            const float bz_n = __ldg(A.bz + idxp);
-            f2 f = df_add(f2{__ldg(A.bh + idx), __ldg(A.bl + idx)}, mdf);
+            L.w[0] = __ldg(A.bx + idx);
+            L.w[1] = __ldg(A.bx + idx + o[1]);
+            L.w[2] = __ldg(A.by + idx);
+            L.w[3] = __ldg(A.by + idx + o[3]);
+            L.ph = __ldg(xh + idxp);
+            L.pl = __ldg(xl + idxp);
+            L.bzn = __ldg(A.bz + idxp);
+            L.bh = __ldg(A.bh + idx);
+            L.bl = __ldg(A.bl + idx);
+        };
+        auto apply = [&](int k, const Ld& L) {
+            const int idx = k * sz + col;
+            f2 f = df_add(f2{L.bh, L.bl}, mdf);
             if (!pos) f = df_neg(f);
             float S = 0.f, c = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) df_face_term(w[q], ch, cl, nh[q], nl[q], S, c);
+            for (int q = 0; q < 4; ++q) df_face_term(L.w[q], ch, cl, L.nh[q], L.nl[q], S, c);
             df_face_term(bz_c, ch, cl, mh, ml, S, c);
-            df_face_term(bz_n, ch, cl, ph_, pl_, S, c);
+            df_face_term(L.bzn, ch, cl, L.ph, L.pl, S, c);
             const f2 ax = f2_mul(two_sum(S, c), ih2);
             const f2 rv = df_add(f, df_neg(ax));
             const float rt = __fadd_rn(rv.hi, rv.lo);
@@ -696,9 +705,23 @@ __global__ void __launch_bounds__(256) k_ir_residual3d(IRArgs A) {
             rr += rt * rt;
             mh = ch;
             ml = cl;
-            ch = ph_;
-            cl = pl_;
-            bz_c = bz_n;
+            ch = L.ph;
+            cl = L.pl;
+            bz_c = L.bzn;
+        };
+        // two planes per round: all loads of both before the arithmetic
+        int k = z0;
+        for (; k + 1 < z1; k += 2) {
+            Ld a, b;
+            load(k, a);
+            load(k + 1, b);
+            apply(k, a);
+            apply(k + 1, b);
+        }
+        if (k < z1) {
+            Ld a;
+            load(k, a);
+            apply(k, a);
         }
     }
     double v[3] = {double(ff), double(rr), double(rr)}, tot[3];

@@ -289,6 +289,8 @@ def run_batch(args, rank, world, local_rank):
     plist, desc = workload(args.workload)
     total_cells = sum(int(np.prod([c for c in p["n"]])) for p in plist)
     mine = deal(plist, rank, world)
+    if args.graph:
+        mine = [dict(p, use_graph=1) for p in mine]
     bat = pf.Batch(mine, nthreads=args.threads)
     bat.step(args.warmup)
 
@@ -318,7 +320,10 @@ def run_batch(args, rank, world, local_rank):
             "scaling": "strong" if world > 1 else "weak",
             "vs_baseline": None, "dtype": "f64" if "fp64" in args.workload else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": desc, "cells": total_cells, "threads": args.threads,
+            "config": {"workload": desc, "cells": total_cells,
+                       "threads": 1 if args.graph else args.threads,
+                       "execution": "one captured CUDA graph per instance step, device-driven "
+                                    "solver loops" if args.graph else "host-driven, thread pool",
                        "parallelism": f"instances dealt to {world} ranks" if world > 1
                        else "single",
                        "timing": "host wall clock between device synchronisations, max over ranks"},
@@ -469,6 +474,9 @@ def main():
                     help="relative reduction of each float32 inner solve (mixed path)")
     ap.add_argument("--mg-sweeps", type=int, default=None,
                     help="pre- and post-smoothing sweeps per V-cycle (tuning; default 1)")
+    ap.add_argument("--graph", type=int, default=None,
+                    help="1: replay one captured CUDA graph per step (use_graph); "
+                         "default 1 for the batch workloads, 0 otherwise")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -478,6 +486,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.graph is None:
+        args.graph = 1 if args.workload.startswith("batch") else 0
     if args.workload.startswith("batch"):
         run_batch(args, rank, world, local_rank)
         return

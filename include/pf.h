@@ -93,7 +93,11 @@ typedef struct {
     double bound_tol;     /* > 0: flag PF_ERR_UNBOUNDED when phi leaves [-tol, 1 + tol] */
     double inner_tol;     /* mixed precision: relative residual reduction of each float32
                              inner solve between float64 refinements (0: 1e-6) */
-    int reserved[8];      /* must be zero */
+    int use_graph;        /* 1: pf_step replays one CUDA graph per step (captured at the first
+                             pf_step), the pressure solves' CG and refinement loops as
+                             device-driven WHILE nodes; no host round trips inside a step.
+                             Same results as 0 (host-driven loops). */
+    int reserved[7];      /* must be zero */
 } pf_params;
 
 typedef struct {
@@ -219,7 +223,10 @@ pf_status pf_poisson_solve_static(const pf_params* prm, const double* phi, const
  * blocking waits, so the kernels of different instances overlap on the GPU.
  * Each instance computes exactly what pf_step computes on its own context.
  * The library creates (and pf_batch_destroy destroys) one stream per instance;
- * it allocates no device memory. pf_batch_context gives the context of
+ * it allocates no device memory. When every instance has use_graph = 1, one
+ * host thread instead enqueues the captured step graphs of all instances on
+ * their streams and then waits for them (no host work inside a step).
+ * pf_batch_context gives the context of
  * instance i for pf_get_field / pf_diagnostics (do not pf_destroy it). Returns
  * the first failing instance's status; the text is in pf_batch_last_error. */
 typedef struct pf_batch pf_batch;

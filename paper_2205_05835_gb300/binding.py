@@ -47,7 +47,8 @@ class pf_params(ctypes.Structure):
         ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int),
         ("bound_tol", ctypes.c_double),
         ("inner_tol", ctypes.c_double),
-        ("reserved", ctypes.c_int * 8),
+        ("use_graph", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
     ]
 
 

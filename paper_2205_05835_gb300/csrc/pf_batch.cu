@@ -22,6 +22,7 @@ struct pf_batch {
     std::vector<cudaStream_t> streams;
     std::vector<int> order;      // instances by decreasing cell count
     int nthreads = 1;
+    bool graphs = false;         // every instance replays a captured step graph
     std::string err;
 };
 
@@ -100,6 +101,8 @@ pf_status pf_batch_init(const pf_params* prms, int count, void* workspace, size_
         b->streams.push_back(st);
         off += align256(bi);
     }
+    b->graphs = true;
+    for (int i = 0; i < count; ++i) b->graphs = b->graphs && prms[i].use_graph == 1;
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
@@ -109,7 +112,37 @@ pf_status pf_batch_init(const pf_params* prms, int count, void* workspace, size_
     return PF_OK;
 }
 
+// Graph mode: one host thread enqueues the step-graph replays of every
+// instance on its own stream (largest first), then waits for each; the first
+// steps of instances that have no graph yet run host-driven inside step_begin.
+static pf_status batch_run_graphs(pf_batch* b, int nsteps, const int* each) {
+    const int count = (int)b->ctx.size();
+    int status = PF_OK, failed = -1;
+    std::vector<char> begun(count, 0);
+    for (int t = 0; t < count; ++t) {
+        const int i = b->order[t];
+        const int k = each ? each[i] : nsteps;
+        if (k <= 0) continue;
+        const int s = pf::ctx_step_begin(b->ctx[i], k);
+        begun[i] = 1;
+        if (s != PF_OK && status == PF_OK) { status = s; failed = i; }
+    }
+    for (int t = 0; t < count; ++t) {
+        const int i = b->order[t];
+        if (!begun[i]) continue;
+        const int s = pf::ctx_step_end(b->ctx[i]);
+        if (s != PF_OK && status == PF_OK) { status = s; failed = i; }
+    }
+    if (status != PF_OK) {
+        b->err = "instance " + std::to_string(failed) + ": " + pf_last_error(b->ctx[failed]);
+        return (pf_status)status;
+    }
+    b->err.clear();
+    return PF_OK;
+}
+
 static pf_status batch_run(pf_batch* b, int nsteps, const int* each) {
+    if (b->graphs) return batch_run_graphs(b, nsteps, each);
     const int count = (int)b->ctx.size();
     std::atomic<int> next(0);
     std::atomic<int> status((int)PF_OK);

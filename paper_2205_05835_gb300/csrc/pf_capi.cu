@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/pf.h"
 #include "pf_internal.h"
@@ -32,6 +33,29 @@ struct Carver {
     }
 };
 
+// A CUDA graph assembled from stream-capture segments and conditional nodes:
+// `tail` holds the nodes the next segment or node depends on.
+struct GraphBuilder {
+    cudaGraph_t g = nullptr;
+    std::vector<cudaGraphNode_t> tail;
+    cudaError_t begin(cudaStream_t s) {
+        return cudaStreamBeginCaptureToGraph(s, g, tail.empty() ? nullptr : tail.data(), nullptr,
+                                             tail.size(), cudaStreamCaptureModeRelaxed);
+    }
+    cudaError_t end(cudaStream_t s) {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+        std::vector<cudaGraphNode_t> t;
+        if (e == cudaSuccess && deps) t.assign(deps, deps + nd);
+        cudaGraph_t out = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &out);
+        if (e == cudaSuccess && e2 == cudaSuccess) tail.swap(t);
+        return e != cudaSuccess ? e : e2;
+    }
+};
+
 const char* kClassNames[KC_COUNT] = {
     "cell_pass", "stage", "gamma", "divergence", "correct", "mg_coarsen_beta", "mg_gs_level0",
     "mg_gs_coarse_levels", "mg_restrict", "mg_prolong", "mg_coarse_vcycle", "ir_residual_f64",
@@ -47,6 +71,8 @@ struct Impl {
     virtual void init_phi(const double* phi0) = 0;
     virtual void zero_state() = 0;
     virtual pf_status step(int nsteps) = 0;
+    virtual pf_status step_begin(int nsteps) = 0;   // graph mode: enqueue only
+    virtual pf_status step_end() = 0;               // graph mode: wait and check
     virtual pf_status project() = 0;
     virtual pf_status diagnostics(pf_diag* out) = 0;
     virtual pf_status get_field(int f, double* dst) = 0;
@@ -148,7 +174,8 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "poisson_rtol must be > 0 and poisson_maxit >= 1";
         return PF_ERR_INVALID;
     }
-    for (int i = 0; i < 8; ++i)
+    if (p->use_graph != 0 && p->use_graph != 1) { why = "use_graph must be 0 or 1"; return PF_ERR_INVALID; }
+    for (int i = 0; i < 7; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
     return PF_OK;
 }
@@ -202,6 +229,10 @@ struct ImplT final : Impl {
     // Pressure of the first projection of an RK4 step (its solve target); the
     // state's pressure p holds the other three in turn (see one_step).
     double* pw = nullptr;
+    // graph mode: the captured step and the builder while capturing
+    cudaGraphExec_t gexec = nullptr;
+    GraphBuilder* gb = nullptr;
+    int pending = 0;          // graph launches enqueued by step_begin
     int last_iters = 0, max_iters = 0;
     double last_relres = 0.0, last_gamma = 0.0;
     int host_status = 0;
@@ -257,6 +288,7 @@ struct ImplT final : Impl {
     cudaEvent_t sleep_ev = nullptr;   // blocking-sync event (batched execution)
 
     ~ImplT() override {
+        if (gexec) cudaGraphExecDestroy(gexec);
         prof.destroy();
         if (sleep_ev) cudaEventDestroy(sleep_ev);
         if (!owns_host) return;
@@ -528,8 +560,40 @@ struct ImplT final : Impl {
 
     // A x = sign (b - mean b): float64 iterative refinement around inner
     // MG-preconditioned CG in T, warm start from x = p
-    pf_status solve(const T* phi, double sign) {
-        SolveIO<T, DIM> io = solve_io(phi, sign);
+    // one inner CG iteration: V-cycle (with the CG dot products fused into its
+    // last sweep where possible), direction and operator product, update.
+    // first < 0: the kernels read "first iteration" from the device counter.
+    void cg_iter(SolveIO<T, DIM>& io, const T* phi, int cur, int first) {
+        SweepDots sd;
+        sd.q = reinterpret_cast<const float*>(qT);
+        sd.rb = rb;
+        sd.sc = sc;
+        sd.first = first;
+        bool dots_done = false;
+        io.z = launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof, &sd, &dots_done);
+        if (!dots_done) {
+            prof.begin(KC_CG_DOTS);
+            launch_in_dots<T, DIM>(g, io, first, rb, sc, st);
+            prof.end();
+        }
+        prof.begin(KC_CG_DIR);
+        if (DIM == 3 && sizeof(T) == sizeof(float) && beta32[0] != nullptr && dir3d_ok(g)) {
+            const float* bl[3] = {beta32[0], beta32[1], beta32[2]};
+            launch_dir3d_reg(g, reinterpret_cast<const float*>(io.z),
+                             reinterpret_cast<const float*>(cur ? pd[1] : pd[0]),
+                             reinterpret_cast<float*>(cur ? pd[0] : pd[1]),
+                             reinterpret_cast<float*>(qT), bl, first, rb, sc, st);
+        } else {
+            launch_in_dir<T, DIM>(g, ph, io, cur, first, rb, sc, st);
+        }
+        prof.end();
+        prof.begin(KC_CG_UPDATE);
+        launch_in_update<T, DIM>(g, io, cur, first, rb, sc, st);
+        prof.end();
+    }
+
+    // operator setup and the first outer residual of a solve
+    void solve_prologue(SolveIO<T, DIM>& io, const T* phi) {
         if (sizeof(T) == sizeof(double)) {
             prof.begin(KC_BETA0);
             launch_beta0<T, DIM>(g, ph, phi, beta64, st);
@@ -545,6 +609,23 @@ struct ImplT final : Impl {
         prof.begin(KC_IR_RESIDUAL);
         launch_ir_residual<T, DIM>(g, ph, io, 1, rb, sc, st);
         prof.end();
+    }
+    // x += e and the next outer residual
+    void solve_refine(SolveIO<T, DIM>& io) {
+        prof.begin(KC_IR_ADDCORR);
+        launch_ir_addcorr<T, DIM>(g, io, sc, st);
+        prof.end();
+        prof.begin(KC_IR_RESIDUAL);
+        launch_ir_residual<T, DIM>(g, ph, io, 0, rb, sc, st);
+        prof.end();
+    }
+
+    // A x = sign (b - mean b): float64 iterative refinement around inner
+    // MG-preconditioned CG in T, warm start from x = p
+    pf_status solve(const T* phi, double sign) {
+        if (gb) return solve_captured(phi, sign);
+        SolveIO<T, DIM> io = solve_io(phi, sign);
+        solve_prologue(io, phi);
         pf_status ps = poll();
         if (ps != PF_OK) return ps;
         const int poll_every = 2;
@@ -552,34 +633,7 @@ struct ImplT final : Impl {
         while (!h_sc->done && outer < 64) {
             int cur = 0;
             for (int it = 0; it <= prm.poisson_maxit + poll_every; ++it) {
-                const int first = (it == 0);
-                SweepDots sd;
-                sd.q = reinterpret_cast<const float*>(qT);
-                sd.rb = rb;
-                sd.sc = sc;
-                sd.first = first;
-                bool dots_done = false;
-                io.z = launch_vcycle<T, DIM>(ph, phi, H, sc, st, &prof, &sd, &dots_done);
-                if (!dots_done) {
-                    prof.begin(KC_CG_DOTS);
-                    launch_in_dots<T, DIM>(g, io, first, rb, sc, st);
-                    prof.end();
-                }
-                prof.begin(KC_CG_DIR);
-                if (DIM == 3 && sizeof(T) == sizeof(float) && beta32[0] != nullptr &&
-                    dir3d_ok(g)) {
-                    const float* bl[3] = {beta32[0], beta32[1], beta32[2]};
-                    launch_dir3d_reg(g, reinterpret_cast<const float*>(io.z),
-                                 reinterpret_cast<const float*>(cur ? pd[1] : pd[0]),
-                                 reinterpret_cast<float*>(cur ? pd[0] : pd[1]),
-                                 reinterpret_cast<float*>(qT), bl, first, rb, sc, st);
-                } else {
-                    launch_in_dir<T, DIM>(g, ph, io, cur, first, rb, sc, st);
-                }
-                prof.end();
-                prof.begin(KC_CG_UPDATE);
-                launch_in_update<T, DIM>(g, io, cur, first, rb, sc, st);
-                prof.end();
+                cg_iter(io, phi, cur, it == 0 ? 1 : 0);
                 cur = 1 - cur;
                 if ((it + 1) % poll_every == 0) {
                     ps = poll();
@@ -587,17 +641,17 @@ struct ImplT final : Impl {
                     if (h_sc->idone || h_sc->done) break;
                 }
             }
-            prof.begin(KC_IR_ADDCORR);
-            launch_ir_addcorr<T, DIM>(g, io, sc, st);
-            prof.end();
-            prof.begin(KC_IR_RESIDUAL);
-            launch_ir_residual<T, DIM>(g, ph, io, 0, rb, sc, st);
-            prof.end();
+            solve_refine(io);
             ps = poll();
             if (ps != PF_OK) return ps;
             ++outer;
         }
         CK(cudaGetLastError());
+        return solve_status();
+    }
+
+    // iteration counts and the latched status of the last solve (h_sc current)
+    pf_status solve_status() {
         last_iters = h_sc->iters;
         if (last_iters > max_iters) max_iters = last_iters;
         last_relres = h_sc->ff > 0 ? sqrt(h_sc->rr / h_sc->ff) : 0.0;
@@ -609,6 +663,98 @@ struct ImplT final : Impl {
             err = stt == PF_ERR_NOT_CONVERGED ? "Poisson solve reached poisson_maxit"
                                               : "non-finite value in the Poisson solve";
             return (pf_status)stt;
+        }
+        return PF_OK;
+    }
+
+    // ---------------- graph capture ----------------
+    // WHILE node in the graph being built: its condition is set by a kernel
+    // just before the node and at the end of every pass of its body (which = 0
+    // inner CG loop, 1 outer refinement loop, see launch_set_cond).
+    template <typename F>
+    pf_status add_while(int which, F body_fn) {
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, gb->g, 0, 0));
+        launch_set_cond(h, sc, which, st);
+        CK(gb->end(st));
+        // (the parameter union has no default constructor: zeroed raw storage)
+        alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+        memset(np_raw, 0, sizeof(np_raw));
+        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, gb->g, gb->tail.empty() ? nullptr : gb->tail.data(), nullptr,
+                            gb->tail.size(), &np));
+        GraphBuilder body;
+        body.g = np.conditional.phGraph_out[0];
+        GraphBuilder* outer = gb;
+        gb = &body;
+        CK(body.begin(st));
+        pf_status s = body_fn();
+        launch_set_cond(h, sc, which, st);
+        cudaError_t e = body.end(st);
+        gb = outer;
+        if (s != PF_OK) return s;
+        CK(e);
+        gb->tail.assign(1, node);
+        CK(gb->begin(st));
+        return PF_OK;
+    }
+
+    // the solve inside a graph: refinement loop around the inner CG loop
+    // (unrolled by two: the direction buffers alternate), both device-driven
+    pf_status solve_captured(const T* phi, double sign) {
+        SolveIO<T, DIM> io = solve_io(phi, sign);
+        solve_prologue(io, phi);
+        return add_while(1, [&]() -> pf_status {
+            pf_status s = add_while(0, [&]() -> pf_status {
+                cg_iter(io, phi, 0, -1);
+                cg_iter(io, phi, 1, -1);
+                return PF_OK;
+            });
+            if (s != PF_OK) return s;
+            solve_refine(io);
+            return PF_OK;
+        });
+    }
+
+    // Capture one step into gexec (kernel attributes are set beforehand: no
+    // such call runs inside the capture).
+    pf_status capture_step() {
+        sweep3d_prepare();
+        // the legacy default stream cannot be captured: record on a private
+        // stream (recording runs nothing); the graph replays on the context's
+        cudaStream_t own = st, rec = nullptr;
+        if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) {
+            CK(cudaStreamSynchronize(st));
+            CK(cudaStreamCreateWithFlags(&rec, cudaStreamNonBlocking));
+            st = rec;
+        }
+        GraphBuilder top;
+        cudaError_t e = cudaGraphCreate(&top.g, 0);
+        const bool timing = prof.timing;
+        prof.timing = false;
+        gb = &top;
+        if (e == cudaSuccess) e = top.begin(st);
+        pf_status s = e == cudaSuccess ? one_step() : PF_ERR_CUDA;
+        if (gb != &top) s = PF_ERR_CUDA;
+        gb = nullptr;
+        cudaError_t e2 = top.g ? top.end(st) : cudaErrorInvalidValue;
+        prof.timing = timing;
+        st = own;
+        if (rec) cudaStreamDestroy(rec);
+        if (s == PF_OK && e == cudaSuccess && e2 == cudaSuccess)
+            e = cudaGraphInstantiate(&gexec, top.g, 0);
+        cudaGraphDestroy(top.g);
+        if (s != PF_OK || e != cudaSuccess || e2 != cudaSuccess) {
+            gexec = nullptr;
+            cudaGetLastError();
+            if (err.empty()) err = std::string("graph capture failed: ") +
+                                   cudaGetErrorString(e != cudaSuccess ? e : e2);
+            return s != PF_OK ? s : PF_ERR_CUDA;
         }
         return PF_OK;
     }
@@ -651,9 +797,14 @@ struct ImplT final : Impl {
                 tape_copy(tape->phi[1], phiA);
                 tape_copy(tape->p[0], p);
             }
-            T* t = phiN;
-            phiN = phiA;
-            phiA = t;
+            if (gb) {
+                // a captured step keeps its buffers: the new phi is copied back
+                tape_copy(phiN, static_cast<const T*>(phiA));
+            } else {
+                T* t = phiN;
+                phiN = phiA;
+                phiA = t;
+            }
             return s;
         }
         T* phin_s[4] = {phiN, phiA, phiB, phiA};
@@ -707,6 +858,11 @@ struct ImplT final : Impl {
     }
 
     pf_status step(int nsteps) override {
+        if (prm.use_graph) {
+            pf_status s = step_begin(nsteps);
+            if (s != PF_OK) return s;
+            return step_end();
+        }
         for (int k = 0; k < nsteps; ++k) {
             pf_status s = one_step();
             if (s != PF_OK) return s;
@@ -718,6 +874,42 @@ struct ImplT final : Impl {
         last_gamma = h_scalar[0];
         CK(cudaGetLastError());
         return PF_OK;
+    }
+
+    // Graph mode: enqueue nsteps replays of the captured step (captured at the
+    // first call); host-driven mode: the steps.
+    pf_status step_begin(int nsteps) override {
+        if (!prm.use_graph) return step(nsteps);
+        if (nsteps <= 0) return PF_OK;
+        if (!gexec) {
+            pf_status s = capture_step();
+            if (s != PF_OK) return s;
+        }
+        for (int k = 0; k < nsteps; ++k) {
+            CK(cudaGraphLaunch(gexec, st));
+            ++nstep;
+            time += prm.dt;
+        }
+        pending += nsteps;
+        return PF_OK;
+    }
+
+    // Waits for the enqueued replays and returns the first latched error of
+    // their solves (non-finite values, iteration cap).
+    pf_status step_end() override {
+        if (!prm.use_graph) return PF_OK;
+        CK(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_scalar, gamma, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (sleep_ev) {
+            CK(cudaEventRecord(sleep_ev, st));
+            CK(cudaEventSynchronize(sleep_ev));
+        } else {
+            CK(cudaStreamSynchronize(st));
+        }
+        CK(cudaGetLastError());
+        last_gamma = h_scalar[0];
+        pending = 0;
+        return solve_status();
     }
 
     pf_status project() override {
@@ -1206,6 +1398,14 @@ pf_status run_static_solve(const pf_params& prm, cudaStream_t st, void* scratch,
 }  // namespace
 
 namespace pf {
+int ctx_step_begin(pf_ctx* ctx, int nsteps) {
+    if (!ctx || nsteps < 0) return PF_ERR_INVALID;
+    return (int)ctx->impl->step_begin(nsteps);
+}
+int ctx_step_end(pf_ctx* ctx) {
+    if (!ctx) return PF_ERR_INVALID;
+    return (int)ctx->impl->step_end();
+}
 int ctx_set_blocking(pf_ctx* ctx, int on) {
     if (!ctx) return PF_ERR_INVALID;
     return (int)ctx->impl->set_blocking(on != 0);

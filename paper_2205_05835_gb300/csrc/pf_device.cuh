@@ -327,6 +327,7 @@ __device__ __forceinline__ void ir_finish(const double (&tot)[3], int first, CGS
     sc->rr0_in = tot[2];
     sc->outer += 1;
     sc->idone = 0;
+    sc->it_in = 0;
     if (!(tot[1] == tot[1])) {
         sc->done = 1;
         sc->status = 4;  // PF_ERR_NONFINITE
@@ -339,6 +340,14 @@ __device__ __forceinline__ void ir_finish(const double (&tot)[3], int first, CGS
         double e2 = sc->rtol2 * ffv / tot[1];
         sc->eta2 = e2 > sc->eta2_min ? e2 : sc->eta2_min;
     }
+}
+
+// First inner CG iteration: given by the launch (f >= 0, host-driven loops) or
+// read from the device counter (f < 0, loops inside a CUDA graph). Every
+// kernel of an iteration reads the counter before that iteration's update
+// kernel advances it.
+__device__ __forceinline__ int first_of(int f, const CGScalars* sc) {
+    return f >= 0 ? f : (sc->it_in == 0 ? 1 : 0);
 }
 
 // One face term of a compensated double-float operator sum: adds

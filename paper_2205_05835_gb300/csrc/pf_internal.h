@@ -107,7 +107,7 @@ struct CGScalars {
     int outer;        // outer residual evaluations of the current / last solve
     int status;       // latched device error (pf_status value), 0 if none
     int capped;       // inner iteration cap reached
-    int pad;
+    int it_in;        // iterations of the current inner solve (device-driven loops)
 };
 
 // One multigrid level of the preconditioner.
@@ -142,6 +142,9 @@ constexpr int kRedPart = 1 << 17;
 
 // One-pass red-black Gauss-Seidel sweep of a 3D float32 level (pf_mg3d.cu).
 bool sweep3d_ok(const Dims& g);
+// Sets the sweep kernels' launch attributes (done by the first launch
+// otherwise); called before a stream capture.
+void sweep3d_prepare();
 long long sweep3d_blocks(const Dims& g);   // CTAs of a tiled sweep / direction kernel
 // dots: also form r.z (r = the level's f, z = x_out) and z.q and set the CG
 // beta / rz scalars (the work of the CG dot kernel), first: no previous q.
@@ -295,6 +298,9 @@ template <typename T, int DIM>
 void launch_in_update(const Dims& g, const SolveIO<T, DIM>& io, int cur, int first, RedBuf rb,
                       CGScalars* sc, cudaStream_t s);
 void launch_sum(int n, const double* x, RedBuf rb, double* out, cudaStream_t s);
+// Sets the condition of a WHILE node of a captured solve (which = 0: inner CG
+// loop, 1: outer refinement loop) from the solve's device scalars.
+void launch_set_cond(cudaGraphConditionalHandle h, const CGScalars* sc, int which, cudaStream_t s);
 // The mixed path keeps the pressure and the projection's right-hand side as
 // double-floats: n float hi parts followed by n float lo parts, in the 8 n
 // bytes of a float64 array of n entries.
@@ -366,4 +372,8 @@ struct pf_ctx;
 namespace pf {
 // Make the context's host waits sleep on a blocking-sync event (pf_capi.cu).
 int ctx_set_blocking(pf_ctx* ctx, int on);
+// Graph mode: enqueue nsteps captured steps without waiting / wait for them and
+// return the latched status (host-driven contexts: step_begin runs the steps).
+int ctx_step_begin(pf_ctx* ctx, int nsteps);
+int ctx_step_end(pf_ctx* ctx);
 }  // namespace pf

@@ -128,6 +128,7 @@ __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* 
     float* const Cs = &S.c[0][0][0];
     float* const Ns = &S.n[0][0][0];
     float rz = 0.f, zq = 0.f;   // per-thread partial dots (A.dots)
+    const int first_it = A.dots ? first_of(A.first, A.scw) : 1;
 
     const Dims& g = A.g;
     const int tid = threadIdx.x;
@@ -249,7 +250,7 @@ __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* 
         }
     }
     // q of the second-colour cells (fused dots), loaded one plane ahead
-    const bool want_q = A.dots && !A.first && !first_grp;
+    const bool want_q = A.dots && !first_it && !first_grp;
     float2 qv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     if (want_q && z0 < z1) {
 #pragma unroll
@@ -352,7 +353,7 @@ __device__ __forceinline__ void sweep3d_body(const SweepArgs& A, unsigned char* 
         const int nb = gridDim.x * gridDim.y * gridDim.z;
         if (grid_reduce_lin<2>(v, mode, A.rb, tot, bid, nb) && threadIdx.x == 0) {
             CGScalars* sc = A.scw;
-            sc->beta = A.first ? 0.0 : -sc->alpha * tot[1] / sc->rz;
+            sc->beta = first_it ? 0.0 : -sc->alpha * tot[1] / sc->rz;
             sc->rz = tot[0];
         }
     }
@@ -367,20 +368,25 @@ __global__ void __launch_bounds__(NT, FROM_PHI ? 6 : 4) k_sweep3d(SweepArgs A, c
     sweep3d_body<FROM_PHI, V>(A, smem_raw);
 }
 
+// dynamic shared memory beyond 48 KB, and a shared-memory carveout that lets
+// several CTAs share an SM (once per process)
 template <bool FROM_PHI, int V>
-void launch_sweep3d_t(const SweepArgs& a, dim3 grid, const CGScalars* sc, cudaStream_t s) {
-    // a zero-start sweep copies no x_in: its launch leaves out the x ring
-    using SM = Smem<FROM_PHI, V>;
-    const size_t bytes = a.xin == nullptr ? offsetof(SM, x) : sizeof(SM);
+void sweep3d_attributes() {
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
-        // dynamic shared memory beyond 48 KB, and a shared-memory carveout that
-        // lets several CTAs share an SM
         cudaFuncSetAttribute(k_sweep3d<FROM_PHI, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(Smem<FROM_PHI, V>));
         cudaFuncSetAttribute(k_sweep3d<FROM_PHI, V>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     });
+}
+
+template <bool FROM_PHI, int V>
+void launch_sweep3d_t(const SweepArgs& a, dim3 grid, const CGScalars* sc, cudaStream_t s) {
+    // a zero-start sweep copies no x_in: its launch leaves out the x ring
+    using SM = Smem<FROM_PHI, V>;
+    const size_t bytes = a.xin == nullptr ? offsetof(SM, x) : sizeof(SM);
+    sweep3d_attributes<FROM_PHI, V>();
     k_sweep3d<FROM_PHI, V><<<grid, NT, bytes, s>>>(a, sc);
 }
 
@@ -398,6 +404,12 @@ int tiled_zc(const Dims& g) {
 long long sweep3d_blocks(const Dims& g) {
     const int zc = tiled_zc(g);
     return (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * ((g.nz + zc - 1) / zc);
+}
+
+void sweep3d_prepare() {
+    sweep3d_attributes<true, 4>();
+    sweep3d_attributes<true, 2>();
+    sweep3d_attributes<false, 2>();
 }
 
 // Eligible: 3D float level with even sizes.
@@ -493,7 +505,8 @@ __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
     CGScalars* sc = A.sc;
     if (sc->done || sc->idone) return;
     const Dims& g = A.g;
-    const float bcg = A.first ? 0.f : float(sc->beta);
+    const int first_it = first_of(A.first, sc);
+    const float bcg = first_it ? 0.f : float(sc->beta);
     const int i = blockIdx.x * 32 + threadIdx.x % 32;
     const int j = blockIdx.y * 8 + threadIdx.x / 32;
     const int z0 = blockIdx.z * A.zc;
@@ -512,7 +525,7 @@ __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
         const float* __restrict__ bzp = A.bz;
         float* __restrict__ pnew = A.p_new;
         float* __restrict__ qo = A.q;
-        const bool first = A.first;
+        const bool first = first_it != 0;
         auto pn = [&](int idx) {
             const float zv = __ldg(zp + idx);
             return first ? zv : zv + bcg * __ldg(po + idx);

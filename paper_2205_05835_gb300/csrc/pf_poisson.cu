@@ -639,8 +639,9 @@ k_ir_addcorr(Dims g, SolveIO<T, DIM> io, const CGScalars* sc) {
 // rz = r.z ; zq = z.q (previous q) ; beta = -alpha zq / rz_old
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
-k_in_dots(Dims g, SolveIO<T, DIM> io, int first, RedBuf rb, CGScalars* sc) {
+k_in_dots(Dims g, SolveIO<T, DIM> io, int first_arg, RedBuf rb, CGScalars* sc) {
     if (inner_stopped(sc)) return;
+    const int first = first_of(first_arg, sc);
     double rz = 0.0, zq = 0.0;
     for_cells(g, [&](int, int, int, int idx) {
         const double zv = double(io.z[idx]);
@@ -658,8 +659,10 @@ k_in_dots(Dims g, SolveIO<T, DIM> io, int first, RedBuf rb, CGScalars* sc) {
 // p_new = z + beta p_old ; q = A p_new ; alpha = rz / (p.q)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
-k_in_dir(Dims g, Phys ph, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGScalars* sc) {
+k_in_dir(Dims g, Phys ph, SolveIO<T, DIM> io, int cur, int first_arg, RedBuf rb,
+         CGScalars* sc) {
     if (inner_stopped(sc)) return;
+    const int first = first_of(first_arg, sc);
     const T beta = first ? T(0) : T(sc->beta);
     const T* __restrict__ po = cur ? io.p[1] : io.p[0];
     T* __restrict__ pn = cur ? io.p[0] : io.p[1];
@@ -712,8 +715,9 @@ k_in_dir(Dims g, Phys ph, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGS
 // e += alpha p ; r -= alpha q ; ||r||^2 ; inner stopping test
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
-k_in_update(Dims g, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGScalars* sc) {
+k_in_update(Dims g, SolveIO<T, DIM> io, int cur, int first_arg, RedBuf rb, CGScalars* sc) {
     if (inner_stopped(sc)) return;
+    const int first = first_of(first_arg, sc);
     const T alpha = T(sc->alpha);
     const T* __restrict__ pn = cur ? io.p[0] : io.p[1];
     T rr = T(0);   // per-thread partial in T, float64 across threads
@@ -762,6 +766,7 @@ k_in_update(Dims g, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGScalars
     if (grid_reduce<1>(v, mode, rb, tot) && threadIdx.x == 0) {
         sc->rr_in = tot[0];
         sc->iters += 1;
+        sc->it_in += 1;
         if (!(tot[0] == tot[0])) {
             sc->idone = 1;
         } else if (tot[0] <= sc->eta2 * sc->rr0_in) {
@@ -771,6 +776,20 @@ k_in_update(Dims g, SolveIO<T, DIM> io, int cur, int first, RedBuf rb, CGScalars
             sc->capped = 1;
         }
     }
+}
+
+// Condition of a WHILE node of a solve captured in a CUDA graph: which = 0
+// inner CG loop (runs while the inner solve has not stopped), which = 1 outer
+// refinement loop (runs while the solve has not converged or stopped; at most
+// 64 outer residuals, as in the host-driven loop).
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const CGScalars* sc, int which) {
+    unsigned v;
+    if (which == 0) v = (sc->done || sc->idone) ? 0u : 1u;
+    else v = (!sc->done && sc->outer < 64) ? 1u : 0u;
+    cudaGraphSetConditional(h, v);
+}
+void launch_set_cond(cudaGraphConditionalHandle h, const CGScalars* sc, int which, cudaStream_t s) {
+    k_set_cond<<<1, 1, 0, s>>>(h, sc, which);
 }
 
 template <typename T, int DIM>

@@ -167,9 +167,9 @@ class ClockSampler:
 # DRAM bytes per cell per launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 256^3 case of the same kernel, mean of the
 # pre- and post-smoothing launches (profiles/k_sweep3d_finest_osc256_mixed.md:
-# 10.9 and 20.2 B/cell); scaled to a launch by the cell count. Valid for the
+# 10.7 and 15.7 B/cell); scaled to a launch by the cell count. Valid for the
 # kernel as profiled; None for every other class.
-NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 15.55}
+NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 13.2}
 
 
 def deal(items, rank, world):

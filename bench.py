@@ -161,14 +161,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Algorithmic bytes per cell and launch of each kernel class on the mixed 3D
-# path (float32 fields and face coefficients, float64 pressure and divergence;
-# derivation in the design doc).
 # DRAM bytes per cell per launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the 256^3 case of the same kernel, mean of the
-# pre- and post-smoothing launches (profiles/k_sweep3d_finest_osc256_mixed.md:
-# 10.7 and 15.7 B/cell); scaled to a launch by the cell count. Valid for the
-# kernel as profiled; None for every other class.
+# dram__bytes_write.sum) on the 256^3 case of the finest sweep, mean of the
+# pre- and post-smoothing launches (10.7 and 15.7 B/cell); scaled to a launch
+# by the cell count. Valid for the kernel as profiled; None for every other
+# class.
 NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 13.2}
 
 
@@ -202,9 +199,9 @@ def algo_bytes_per_cell(cls, dim, w):
         "cg_update": 6 * w,
         # r.z, z.q: read z, r, q
         "cg_dots": 3 * w,
-        # r = f - A x in float64 (mixed: expanded form): read x, b, the float64
-        # copies of the d face arrays and their per-cell sum; write r
-        "ir_residual_f64": 16 + 8 * d + 8 + w if w == 4 else 16 + d * w + w,
+        # r = f - A x to float64 accuracy: read x and b (float64, or double-float
+        # pairs on the mixed path), the d face arrays; write r
+        "ir_residual_f64": 16 + d * w + w,
         # stage kernel: read phi_s, u_s, phi^n, u^n, normals, mu, accumulators;
         # write phi, u*, accumulators (stages 1-2; the first and last move less)
         "stage": (1 + d + 1 + d + d + 1 + 1 + d) * w + (1 + d + 1 + d) * w,

@@ -39,10 +39,12 @@ from scipy.special import eval_legendre
 MODEL_CDI, MODEL_SB, MODEL_ISODI = 0, 1, 2
 FORCE_EB, FORCE_CSF, FORCE_LCSF = 0, 1, 2
 SCHEME_RK4, SCHEME_FE = 0, 1
+MOMENTUM_ADVECTIVE, MOMENTUM_CONSISTENT = 0, 1
 
 _MODELS = {"cdi": 0, "sb": 1, "isodi": 2}
 _FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 _SCHEMES = {"rk4": 0, "fe": 1}
+_MOMENTUM = {"advective": 0, "consistent": 1}
 
 # Projected RK4 (classical tableau): stage time fractions and weights.
 RK4_C = (0.0, 0.5, 0.5, 1.0)
@@ -86,7 +88,8 @@ def S(a, g, d, k):
 def params_from(p):
     """Normalise a parameter dict (names from pf_inputs) to oracle form."""
     q = dict(p)
-    for key, table in (("model", _MODELS), ("force", _FORCES), ("scheme", _SCHEMES)):
+    for key, table in (("model", _MODELS), ("force", _FORCES), ("scheme", _SCHEMES),
+                       ("momentum", _MOMENTUM)):
         if isinstance(q.get(key), str):
             q[key] = table[q[key]]
     return q
@@ -316,6 +319,80 @@ def momentum_rhs(phi, u, g, p):
 
 
 # ----------------------------------------------------------------------------
+# consistent (conservative) momentum transport
+# ----------------------------------------------------------------------------
+def cdi_face_flux(phi, u, g, p, gamma, d):
+    """CDI flux through the d-faces, u phi_f - gamma [eps dphi - phi_f (1 - phi_f) n_f]
+    (the flux whose divergence is the CDI phase-field right-hand side, Table 1)."""
+    n, _ = normals(phi, g, p["delta_n"])
+    pf = face_avg(phi, g, d)
+    nf = face_avg(n[d], g, d)
+    return u[d] * pf - gamma * (p["eps"] * face_diff(phi, g, d) - pf * (1.0 - pf) * nf)
+
+
+def mass_flux(phi, u, g, p, gamma):
+    """Mass flux through the d-faces consistent with the CDI phase field.
+
+    With rho = rho_out + (rho_in - rho_out) phi and d phi/dt = -sum_d dF_d/dx_d,
+    the density obeys d rho/dt = -sum_d dm_d/dx_d with
+    m_d = rho_out u_d + (rho_in - rho_out) F_d (exactly, where 0 <= phi <= 1).
+    """
+    drho = p["rho_in"] - p["rho_out"]
+    return [p["rho_out"] * u[d] + drho * cdi_face_flux(phi, u, g, p, gamma, d)
+            for d in range(g.dim)]
+
+
+def momentum_rhs_consistent(phi, u, g, p, gamma):
+    """d(rho_f u_d)/dt without pressure on the d-faces, conservative form:
+       -div(m u_d) + div(eta (grad u + grad u^T))_d + F_d,
+    m the mass flux consistent with the phase field (mass_flux).
+
+    The momentum flux of u_d along d lives at cell centres: mean of m_d over the
+    cell's two d-faces times the mean of u_d over them. Along e != d it lives at
+    the edge between cells i, i-d, i-e, i-d-e: mean of m_e over the e-faces of
+    cells i and i-d times the mean of u_d over the d-faces of cells i and i-e.
+    The viscous stress and the surface force are those of momentum_rhs, not
+    divided by rho_f. The paper defers this transport to its reference
+    [Mirjalili 2021]; this discrete form is a reading.
+    """
+    if p["model"] != MODEL_CDI:
+        raise ValueError("consistent momentum transport needs the CDI model")
+    h = g.h
+    m = mass_flux(phi, u, g, p, gamma)
+    eta = viscosity_cells(phi, p)
+    F = surface_force(phi, g, p)
+    out = []
+    for d in range(g.dim):
+        ud = u[d]
+        adv = np.zeros_like(ud)
+        for e in range(g.dim):
+            if e == d:
+                flux = 0.5 * (m[d] + S(m[d], g, d, 1)) * 0.5 * (ud + S(ud, g, d, 1))
+                adv = adv + (flux - S(flux, g, d, -1)) / h
+            else:
+                flux = 0.5 * (m[e] + S(m[e], g, d, -1)) * 0.5 * (ud + S(ud, g, e, -1))
+                adv = adv + (S(flux, g, e, 1) - flux) / h
+        visc = np.zeros_like(ud)
+        for e in range(g.dim):
+            if e == d:
+                tau = 2.0 * eta * (S(ud, g, d, 1) - ud) / h
+                visc = visc + (tau - S(tau, g, d, -1)) / h
+            else:
+                eta_e = 0.25 * (eta + S(eta, g, d, -1) + S(eta, g, e, -1)
+                                + S(S(eta, g, d, -1), g, e, -1))
+                tau = eta_e * ((ud - S(ud, g, e, -1)) / h + (u[e] - S(u[e], g, d, -1)) / h)
+                visc = visc + (S(tau, g, e, 1) - tau) / h
+        out.append(-adv + visc + F[d])
+    return out
+
+
+def face_density(phi, g, p):
+    """rho_f on the d-faces: the two-cell mean of the cell densities."""
+    rc = density_cells(phi, p)
+    return [face_avg(rc, g, d) for d in range(g.dim)]
+
+
+# ----------------------------------------------------------------------------
 # projection
 # ----------------------------------------------------------------------------
 def divergence(u, g):
@@ -418,18 +495,41 @@ def step(st, p):
     stage is phi_{s+1} = phi^n + c_{s+1} dt k_s, u_{s+1} = P(u^n + c_{s+1} dt k_s)
     projected with rho(phi_{s+1}); the step ends with
     phi^{n+1} = phi^n + dt sum_s w_s k_s and u^{n+1} = P(u^n + dt sum_s w_s k_s).
-    Gamma is frozen over the step at its value from u^n.
+    Gamma is frozen over the step at its value from u^n. With consistent
+    momentum transport (momentum = 1) the stages advance rho_f u instead:
+    u_{s+1} = P((rho_f^n u^n + c_{s+1} dt k_s) / rho_f(phi_{s+1})), likewise at the end.
     """
     p = params_from(p)
     g = Grid(p["dim"], p["n"], p["L"])
     dt = p["dt"]
     gam = gamma_of(st.u, p)
     phin, un = st.phi, st.u
+    cons = p.get("momentum", MOMENTUM_ADVECTIVE) == MOMENTUM_CONSISTENT
+    if cons:
+        # consistent transport advances rho_f u: the stage velocity is the new
+        # momentum divided by the face density of the new phase field
+        rn = face_density(phin, g, p)
+        vn = [rn[d] * un[d] for d in range(g.dim)]
+
+        def krhs(ph, uu):
+            return momentum_rhs_consistent(ph, uu, g, p, gam)
+
+        def vel(v, ph):
+            r = face_density(ph, g, p)
+            return [v[d] / r[d] for d in range(g.dim)]
+    else:
+        vn = un
+
+        def krhs(ph, uu):
+            return momentum_rhs(ph, uu, g, p)
+
+        def vel(v, ph):
+            return v
     if p["scheme"] == SCHEME_FE:
         kphi = phase_rhs(phin, un, g, p, gam)
-        ku = momentum_rhs(phin, un, g, p)
+        ku = krhs(phin, un)
         phi1 = phin + dt * kphi
-        ustar = [un[d] + dt * ku[d] for d in range(g.dim)]
+        ustar = vel([vn[d] + dt * ku[d] for d in range(g.dim)], phi1)
         u1, pr = project(ustar, phi1, g, p, dt)
         return State(phi1, u1, pr, st.step + 1, st.t + dt)
     phis, us = phin, un
@@ -438,18 +538,18 @@ def step(st, p):
     pr = st.p
     for s in range(4):
         kphi = phase_rhs(phis, us, g, p, gam)
-        ku = momentum_rhs(phis, us, g, p)
+        ku = krhs(phis, us)
         wdt = RK4_W[s] * dt
         if s < 3:
             acc_phi = wdt * kphi if s == 0 else acc_phi + wdt * kphi
             acc_u = [wdt * ku[d] if s == 0 else acc_u[d] + wdt * ku[d] for d in range(g.dim)]
             cdt = RK4_C[s + 1] * dt
             phis = phin + cdt * kphi
-            ustar = [un[d] + cdt * ku[d] for d in range(g.dim)]
+            ustar = vel([vn[d] + cdt * ku[d] for d in range(g.dim)], phis)
             us, pr = project(ustar, phis, g, p, cdt)
         else:
             phi_new = phin + (acc_phi + wdt * kphi)
-            ustar = [un[d] + (acc_u[d] + wdt * ku[d]) for d in range(g.dim)]
+            ustar = vel([vn[d] + (acc_u[d] + wdt * ku[d]) for d in range(g.dim)], phi_new)
             u_new, pr = project(ustar, phi_new, g, p, dt)
             return State(phi_new, u_new, pr, st.step + 1, st.t + dt)
 

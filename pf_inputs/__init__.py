@@ -23,6 +23,7 @@ MODELS = {"cdi": 0, "sb": 1, "isodi": 2}
 FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 SCHEMES = {"rk4": 0, "fe": 1}
+MOMENTUM = {"advective": 0, "consistent": 1}
 
 BATCH_SEED = 20261203
 
@@ -32,7 +33,7 @@ def _base(**kw):
         dim=2, n=(64, 64, 1), L=1.0,
         model="cdi", force="eb", precision="fp64", scheme="rk4",
         sigma=1.0, eps=None, rho_in=1.0, rho_out=1.0, mu_in=0.1, mu_out=0.1,
-        gamma_fixed=0.0, gamma_min=0.0, dt=None, delta_n=1e-12,
+        gamma_fixed=0.0, gamma_min=0.0, dt=None, delta_n=1e-12, momentum="advective",
         poisson_rtol=1e-12, poisson_maxit=200,
         R=0.25, pert_mode=0, pert_amp=0.0, steps=1,
     )
@@ -64,7 +65,9 @@ def suggest_dt(p):
     """
     dx = p["L"] / p["n"][0]
     d = p["dim"]
-    lims = [math.sqrt((p["rho_in"] + p["rho_out"]) * dx ** 3 / (4.0 * math.pi * p["sigma"]))]
+    lims = [0.2 * dx]   # without surface tension: an advective bound for velocities of order 1
+    if p["sigma"] > 0:
+        lims = [math.sqrt((p["rho_in"] + p["rho_out"]) * dx ** 3 / (4.0 * math.pi * p["sigma"]))]
     nu = max(p["mu_in"] / p["rho_in"], p["mu_out"] / p["rho_out"])
     if nu > 0:
         lims.append(dx * dx / (2.0 * d * nu))

@@ -62,6 +62,7 @@ enum { PF_CDI = 0, PF_SB = 1, PF_ISODI = 2 };               /* phase-field model
 enum { PF_FORCE_EB = 0, PF_FORCE_CSF = 1, PF_FORCE_LCSF = 2 }; /* surface tension force */
 enum { PF_FP64 = 0, PF_MIXED = 1 };                         /* precision of stencils and V-cycles */
 enum { PF_RK4_PROJ = 0, PF_FE = 1 };                        /* time integrator */
+enum { PF_MOMENTUM_ADVECTIVE = 0, PF_MOMENTUM_CONSISTENT = 1 }; /* momentum transport */
 enum { PF_FIELD_PHI = 0, PF_FIELD_U = 1, PF_FIELD_V = 2, PF_FIELD_W = 3, PF_FIELD_P = 4 };
 
 typedef struct {
@@ -97,7 +98,14 @@ typedef struct {
                              pf_step), the pressure solves' CG and refinement loops as
                              device-driven WHILE nodes; no host round trips inside a step.
                              Same results as 0 (host-driven loops). */
-    int reserved[7];      /* must be zero */
+    int momentum;         /* PF_MOMENTUM_ADVECTIVE: du/dt = -(u.grad)u + (div tau + F) / rho_f.
+                             PF_MOMENTUM_CONSISTENT (CDI model only): rho_f u advanced in
+                             conservative form, d(rho_f u)/dt = -div(m u) + div tau + F, with
+                             the mass flux m = rho_out u + (rho_in - rho_out) F_CDI consistent
+                             with the phase-field flux (the transport the paper's Section 3
+                             takes from its reference Mirjalili 2021; the discrete form is this
+                             library's). Stage velocities are the new momentum over rho_f. */
+    int reserved[6];      /* must be zero */
 } pf_params;
 
 typedef struct {

@@ -48,7 +48,8 @@ class pf_params(ctypes.Structure):
         ("bound_tol", ctypes.c_double),
         ("inner_tol", ctypes.c_double),
         ("use_graph", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("momentum", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 

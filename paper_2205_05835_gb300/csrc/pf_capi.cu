@@ -175,7 +175,15 @@ pf_status validate(const pf_params* p, std::string& why) {
         return PF_ERR_INVALID;
     }
     if (p->use_graph != 0 && p->use_graph != 1) { why = "use_graph must be 0 or 1"; return PF_ERR_INVALID; }
-    for (int i = 0; i < 7; ++i)
+    if (p->momentum != PF_MOMENTUM_ADVECTIVE && p->momentum != PF_MOMENTUM_CONSISTENT) {
+        why = "bad momentum transport";
+        return PF_ERR_INVALID;
+    }
+    if (p->momentum == PF_MOMENTUM_CONSISTENT && p->model != PF_CDI) {
+        why = "consistent momentum transport needs the CDI model";
+        return PF_ERR_INVALID;
+    }
+    for (int i = 0; i < 6; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
     return PF_OK;
 }
@@ -243,6 +251,7 @@ struct ImplT final : Impl {
         ph.dim = DIM;
         ph.model = prm.model;
         ph.force = prm.force;
+        ph.momentum = prm.momentum;
         ph.sigma = prm.sigma;
         ph.eps = prm.eps;
         ph.rho_in = prm.rho_in;
@@ -513,15 +522,20 @@ struct ImplT final : Impl {
 
     // ---------------- projection ----------------
     // u_out = u_in - tau beta G p with D(beta G p) = D u_in / tau (phi -> rho)
-    pf_status do_project(const T* phi, T* const* uin, double tau, T* const* uout) {
+    // mom: uin holds the momentum rho_f u* of consistent transport (the RK
+    // stages), divided by rho_f(phi) on the fly; else a velocity
+    pf_status do_project(const T* phi, T* const* uin, double tau, T* const* uout,
+                         bool mom = false) {
         const T* uin_c[3] = {uin[0], uin[1], DIM == 3 ? uin[2] : uin[0]};
+        Phys phc = ph;
+        phc.momentum = mom ? 1 : 0;
         prof.begin(KC_DIV);
-        launch_divergence<T, DIM>(g, uin_c, 1.0 / tau, b, rb, sc, st);
+        launch_divergence<T, DIM>(g, uin_c, 1.0 / tau, b, rb, sc, st, mom ? phi : nullptr, &phc);
         prof.end();
         pf_status s = solve(phi, -1.0);
         if (s != PF_OK) return s;
         prof.begin(KC_CORRECT);
-        launch_correct<T, DIM>(g, ph, phi, sizeof(T) == sizeof(double) ? beta64 : nullptr,
+        launch_correct<T, DIM>(g, phc, phi, sizeof(T) == sizeof(double) ? beta64 : nullptr,
                                beta32[0] ? beta32 : nullptr, uin_c, xsolve ? xsolve : p, tau,
                                uout, st);
         prof.end();
@@ -792,7 +806,7 @@ struct ImplT final : Impl {
             prof.begin(KC_STAGE);
             launch_stage<T, DIM>(g, ph, io, 0, 1, dt, dt, 0, st);
             prof.end();
-            pf_status s = do_project(phiA, uStar, dt, uN);
+            pf_status s = do_project(phiA, uStar, dt, uN, prm.momentum == PF_MOMENTUM_CONSISTENT);
             if (tape) {
                 tape_copy(tape->phi[1], phiA);
                 tape_copy(tape->p[0], p);
@@ -838,7 +852,8 @@ struct ImplT final : Impl {
                 launch_extrapolate(g.ncell, sizeof(T) == sizeof(float), pw, p, p, st);
             }
             double* xs = xsolve ? xsolve : p;
-            pf_status ps = do_project(phout[s], uStar, cdt, s < 3 ? uS : uN);
+            pf_status ps = do_project(phout[s], uStar, cdt, s < 3 ? uS : uN,
+                                      prm.momentum == PF_MOMENTUM_CONSISTENT);
             xsolve = nullptr;
             if (ps != PF_OK) return ps;
             if (tape) {
@@ -1123,8 +1138,9 @@ struct ImplT final : Impl {
 
     bool adjoint_supported(std::string& why) const {
         if (sizeof(T) != sizeof(double)) { why = "the adjoint needs precision PF_FP64"; return false; }
-        if (prm.model != PF_CDI || prm.force != PF_FORCE_EB) {
-            why = "the adjoint supports the CDI model with the EB force";
+        if (prm.model != PF_CDI || prm.force != PF_FORCE_EB ||
+            prm.momentum != PF_MOMENTUM_ADVECTIVE) {
+            why = "the adjoint supports the CDI model with the EB force and advective momentum";
             return false;
         }
         return true;
@@ -1573,8 +1589,10 @@ pf_status pf_adjoint_workspace_size(const pf_params* prm, size_t* bytes) {
     pf_status s = validate(prm, why);
     if (s != PF_OK) { g_init_error = why; return s; }
     if (!bytes) { g_init_error = "bytes is NULL"; return PF_ERR_INVALID; }
-    if (prm->precision != PF_FP64 || prm->model != PF_CDI || prm->force != PF_FORCE_EB) {
-        g_init_error = "the adjoint supports precision PF_FP64 with the CDI model and the EB force";
+    if (prm->precision != PF_FP64 || prm->model != PF_CDI || prm->force != PF_FORCE_EB ||
+        prm->momentum != PF_MOMENTUM_ADVECTIVE) {
+        g_init_error = "the adjoint supports precision PF_FP64 with the CDI model, the EB force and "
+                       "advective momentum";
         return PF_ERR_INVALID;
     }
     std::string err;

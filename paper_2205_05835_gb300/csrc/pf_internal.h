@@ -50,6 +50,7 @@ __host__ __device__ inline double ih2_of(const Dims& g, double) { return g.ih2; 
 // converts a double per cell (conversions run on GB300's narrow float64 pipe).
 struct Phys {
     int dim, model, force;
+    int momentum;                         // 0 advective, 1 consistent (conservative) transport
     double sigma, eps, rho_in, rho_out, mu_in, mu_out, delta_n;
     double drho, dmu;                     // rho_in - rho_out, mu_in - mu_out
     float sigma_f, eps_f, rho_out_f, drho_f, mu_out_f, dmu_f, delta_n_f;
@@ -241,9 +242,12 @@ template <typename T, int DIM>
 void launch_correct(const Dims& g, const Phys& ph, const T* phi, const double* const* beta64,
                     const float* const* beta32, const T* const* ustar, const double* p,
                     double tau, T* const* uout, cudaStream_t s);
+// b = D u / tau; with mom_phi != nullptr, u holds momenta rho_f u and is
+// divided by the face densities of mom_phi first (consistent transport).
 template <typename T, int DIM>
 void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double* b, RedBuf rb,
-                       CGScalars* sc, cudaStream_t s);
+                       CGScalars* sc, cudaStream_t s, const T* mom_phi = nullptr,
+                       const Phys* ph = nullptr);
 template <typename T, int DIM>
 void launch_diagnostics(const Dims& g, const Phys& ph, const T* phi, const T* const* u,
                         const double* p, RedBuf rb, DiagOut* out, cudaStream_t s);

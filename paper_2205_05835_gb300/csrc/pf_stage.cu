@@ -26,6 +26,15 @@ __device__ __forceinline__ T eta_of(T phi, const PC<T>& c) {
     return c.mu_out + c.dmu * clamp01(phi);
 }
 
+// velocity from the momentum rho_f u on the face between cells a and b
+// (consistent transport): rho_f from clip(phi) as everywhere, IEEE division
+// in float64, the correctly rounded reciprocal in float32
+template <typename T>
+__device__ __forceinline__ T mom_to_vel(T mom, T pa, T pb, const Phys& ph) {
+    const PC<T> c = pc_of(ph, T());
+    return divq(mom, T(0.5) * (rho_of(pa, c) + rho_of(pb, c)));
+}
+
 // psi'(phi) = phi (1 - phi) (1 - 2 phi), always evaluated in float64.
 __device__ __forceinline__ double dpsi64(double p) { return p * (1.0 - p) * (1.0 - 2.0 * p); }
 
@@ -258,19 +267,61 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
         const int im = nb.ax(d, -1);
         const T pm = ldg(phi, im);
         const T udc = ldg(ud, idx);
-        // advection -(u.grad) u_d, central, transverse components from 4 faces
         T adv = T(0);
+        if (ph.momentum == 0) {
+            // advection -(u.grad) u_d, central, transverse components from 4 faces
 #pragma unroll
-        for (int e = 0; e < DIM; ++e) {
-            T vel;
-            if (e == d) {
-                vel = udc;
-            } else {
-                const T* __restrict__ ue = io.u_s[e];
-                vel = T(0.25) * (ldg(ue, idx) + ldg(ue, nb.ax(e, 1)) + ldg(ue, im) +
-                                 ldg(ue, nb.ax2(d, -1, e, 1)));
+            for (int e = 0; e < DIM; ++e) {
+                T vel;
+                if (e == d) {
+                    vel = udc;
+                } else {
+                    const T* __restrict__ ue = io.u_s[e];
+                    vel = T(0.25) * (ldg(ue, idx) + ldg(ue, nb.ax(e, 1)) + ldg(ue, im) +
+                                     ldg(ue, nb.ax2(d, -1, e, 1)));
+                }
+                adv = adv + vel * ((ldg(ud, nb.ax(e, 1)) - ldg(ud, nb.ax(e, -1))) * inv2h);
             }
-            adv = adv + vel * ((ldg(ud, nb.ax(e, 1)) - ldg(ud, nb.ax(e, -1))) * inv2h);
+        } else {
+            // consistent transport: div(m u_d) in flux form, m the mass flux
+            // rho_out u + (rho_in - rho_out) F of the CDI phase-field flux F
+            // through the face of cell j along dd (cells j and jm = j - e_dd)
+            auto mfl = [&](int dd, int j, int jm) -> T {
+                const T pj = ldg(phi, j), pjm = ldg(phi, jm);
+                const T pf = T(0.5) * (pj + pjm);
+                const T nf = T(0.5) * (ldg(io.nrm[dd], j) + ldg(io.nrm[dd], jm));
+                const T uj = ldg(io.u_s[dd], j);
+                const T F = uj * pf - gam * (eps * ((pj - pjm) * inv_h) - pf * (T(1) - pf) * nf);
+                return pcs.rho_out * uj + pcs.drho * F;
+            };
+            auto cell = [&](int o1, int e1, int o2, int e2) {   // c + o1 e_e1 + o2 e_e2
+                int o[3] = {0, 0, 0};
+                o[e1] += o1;
+                o[e2] += o2;
+                return nb.at(o[0], o[1], o[2]);
+            };
+#pragma unroll
+            for (int e = 0; e < DIM; ++e) {
+                if (e == d) {
+                    // along d: flux at the cells c - e_d and c (their two d-faces)
+                    const int ip = nb.ax(d, 1), im2 = nb.ax(d, -2);
+                    const T m_lo = mfl(d, im, im2), m_c = mfl(d, idx, im), m_hi = mfl(d, ip, idx);
+                    const T u_lo = ldg(ud, im), u_hi = ldg(ud, ip);
+                    const T c_hi = T(0.5) * (m_c + m_hi) * (T(0.5) * (udc + u_hi));
+                    const T c_lo = T(0.5) * (m_lo + m_c) * (T(0.5) * (u_lo + udc));
+                    adv = adv + (c_hi - c_lo) * inv_h;
+                } else {
+                    // along e: flux at the edges below and above the face (cells
+                    // j, j - e_d, j - e_e, j - e_d - e_e for edge j = c, c + e_e)
+                    const int jme = nb.ax(e, -1), jmde = cell(-1, d, -1, e);
+                    const int jpe = nb.ax(e, 1), jpemd = cell(1, e, -1, d);
+                    const T me_lo = T(0.5) * (mfl(e, idx, jme) + mfl(e, im, jmde));
+                    const T me_hi = T(0.5) * (mfl(e, jpe, idx) + mfl(e, jpemd, im));
+                    const T e_lo = me_lo * (T(0.5) * (udc + ldg(ud, jme)));
+                    const T e_hi = me_hi * (T(0.5) * (ldg(ud, jpe) + udc));
+                    adv = adv + (e_hi - e_lo) * inv_h;
+                }
+            }
         }
         // viscous stress divergence
         T visc = T(0);
@@ -311,8 +362,12 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
                 F = T(6) * sigma * kf * pf * (T(1) - pf) * dphi;
             }
         }
-        const T beta = divq(T(1), T(0.5) * (rho_of(pc, pcs) + rho_of(pm, pcs)));
-        ku[d] = -adv + beta * visc + beta * F;
+        if (ph.momentum == 0) {
+            const T beta = divq(T(1), T(0.5) * (rho_of(pc, pcs) + rho_of(pm, pcs)));
+            ku[d] = -adv + beta * visc + beta * F;
+        } else {
+            ku[d] = -adv + visc + F;   // d(rho_f u_d)/dt
+        }
     }
     (void)h;
 
@@ -324,10 +379,26 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
     }
     // ---------------- RK stage update ----------------
     const T phin = ldg(io.phi_n, idx);
+    // advective: the stages advance u from u^n; consistent: they advance
+    // rho_f u from rho_f(phi^n) u^n, which needs phi^n of the neighbour. The
+    // last RK4 stage writes phi^{n+1} over phi^n in place, so there the
+    // momentum of the step start is not re-formed: the consistent
+    // accumulator carries it from stage 0 on.
+    const bool cons = ph.momentum == 1;
+    T vn[3];
+    if (scheme == 1 || stage < 3) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            vn[d] = ldg(io.u_n[d], idx);
+            if (cons)
+                vn[d] = T(0.5) * (rho_of(phin, pcs) + rho_of(ldg(io.phi_n, nb.ax(d, -1)), pcs)) *
+                        vn[d];
+        }
+    }
     if (scheme == 1) {  // forward Euler
         io.phi_out[idx] = phin + cdt * kphi;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) io.u_out[d][idx] = ldg(io.u_n[d], idx) + cdt * ku[d];
+        for (int d = 0; d < DIM; ++d) io.u_out[d][idx] = vn[d] + cdt * ku[d];
         return;
     }
     if (stage < 3) {
@@ -336,15 +407,17 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
         io.phi_out[idx] = phin + cdt * kphi;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            T au = stage == 0 ? wdt * ku[d] : io.acc_u[d][idx] + wdt * ku[d];
+            T au = stage == 0 ? (cons ? vn[d] + wdt * ku[d] : wdt * ku[d])
+                              : io.acc_u[d][idx] + wdt * ku[d];
             io.acc_u[d][idx] = au;
-            io.u_out[d][idx] = ldg(io.u_n[d], idx) + cdt * ku[d];
+            io.u_out[d][idx] = vn[d] + cdt * ku[d];
         }
     } else {
         io.phi_out[idx] = phin + (io.acc_phi[idx] + wdt * kphi);
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-            io.u_out[d][idx] = ldg(io.u_n[d], idx) + (io.acc_u[d][idx] + wdt * ku[d]);
+            io.u_out[d][idx] = cons ? io.acc_u[d][idx] + wdt * ku[d]
+                                    : ldg(io.u_n[d], idx) + (io.acc_u[d][idx] + wdt * ku[d]);
     }
     });
 }
@@ -518,6 +591,11 @@ template <typename T, int DIM>
 void launch_stage(const Dims& g, const Phys& ph, const StageIO<T>& io, int stage, int scheme,
                   double wdt, double cdt, int write_rhs, cudaStream_t s) {
     if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        if (ph.momentum == 1) {
+            k_stage<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
+                g, ph, io, stage, scheme, T(wdt), T(cdt), write_rhs);
+            return;
+        }
         const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
         int zc = 64;
         while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
@@ -564,13 +642,47 @@ void launch_gamma(const Dims& g, const T* const* u, double gamma_fixed, double g
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
-             double inv_tau, double* __restrict__ b, RedBuf rb, CGScalars* sc) {
+             double inv_tau, double* __restrict__ b, RedBuf rb, CGScalars* sc,
+             const T* __restrict__ mphi, Phys ph) {
     double s = 0.0;
     const double inv_h = g.ih;
     f2 acc{0.f, 0.f};
     const f2 scale = sizeof(T) == sizeof(float) ? df_of(inv_h * inv_tau) : f2{0.f, 0.f};
     for_cells(g, [&](int i, int j, int k, int idx) {
         const Nb6 nb = nb6<DIM>(g, i, j, k, idx);
+        if (mphi != nullptr) {
+            // consistent transport: u* = (rho_f u*) / rho_f, formed as in k_correct
+            const T* uu[3] = {u0, u1, u2};
+            T v[3][2];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                v[d][0] = mom_to_vel<T>(uu[d][idx], mphi[idx], mphi[nb.m[2 * d]], ph);
+                v[d][1] = mom_to_vel<T>(uu[d][nb.m[2 * d + 1]], mphi[nb.m[2 * d + 1]], mphi[idx], ph);
+            }
+            if constexpr (sizeof(T) == sizeof(double)) {
+                double dv = (double(v[0][1]) - double(v[0][0])) * inv_h;
+                dv += (double(v[1][1]) - double(v[1][0])) * inv_h;
+                if (DIM == 3) dv += (double(v[2][1]) - double(v[2][0])) * inv_h;
+                dv *= inv_tau;
+                b[idx] = dv;
+                s += dv;
+            } else {
+                f2 t = two_sum(float(v[0][1]), -float(v[0][0]));
+#pragma unroll
+                for (int d = 1; d < DIM; ++d) {
+                    const f2 c1 = two_sum(float(v[d][1]), -float(v[d][0]));
+                    f2 t2 = two_sum(t.hi, c1.hi);
+                    t2.lo = __fadd_rn(t2.lo, __fadd_rn(t.lo, c1.lo));
+                    t = t2;
+                }
+                const f2 r = f2_mul(t, scale);
+                float* bf = reinterpret_cast<float*>(b);
+                bf[idx] = r.hi;
+                bf[idx + g.ncell] = r.lo;
+                acc = df_add(acc, r);
+            }
+            return;
+        }
         if (sizeof(T) == sizeof(double)) {
             double dv = (double(u0[nb.m[1]]) - double(u0[idx])) * inv_h;
             dv += (double(u1[nb.m[3]]) - double(u1[idx])) * inv_h;
@@ -609,15 +721,17 @@ k_divergence(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T
 
 template <typename T, int DIM>
 void launch_divergence(const Dims& g, const T* const* u, double inv_tau, double* b, RedBuf rb,
-                       CGScalars* sc, cudaStream_t s) {
+                       CGScalars* sc, cudaStream_t s, const T* mom_phi, const Phys* ph) {
     if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
-        if (divergence3d_ok(g)) {
+        if (mom_phi == nullptr && divergence3d_ok(g)) {
             launch_divergence3d(g, u, inv_tau, b, rb, sc, s);
             return;
         }
     }
+    Phys pz;
+    memset(&pz, 0, sizeof(pz));
     k_divergence<T, DIM><<<row_grid(g, kThreads, kRedBlocks), kThreads, 0, s>>>(
-        g, u[0], u[1], DIM == 3 ? u[2] : u[0], inv_tau, b, rb, sc);
+        g, u[0], u[1], DIM == 3 ? u[2] : u[0], inv_tau, b, rb, sc, mom_phi, ph ? *ph : pz);
 }
 
 // ---------------------------------------------------------------------------
@@ -643,10 +757,13 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const int m = nb.m[2 * d];
+            // consistent transport: s holds rho_f u*, formed into u* as in k_divergence
+            const T us = ph.momentum == 1 ? mom_to_vel<T>(sv[d][idx], phi[idx], phi[m], ph)
+                                          : sv[d][idx];
             if (b0 != nullptr) {
                 // float64 path: the solver's float64 face coefficients
                 const double gp = (pp - p[m]) * inv_h;
-                ov[d][idx] = T(double(sv[d][idx]) - tau * bv[d][idx] * gp);
+                ov[d][idx] = T(double(us) - tau * bv[d][idx] * gp);
             } else {
                 // float32 path: same beta as the pressure operator; the pressure
                 // is a double-float (hi plane, lo plane), its difference formed
@@ -657,7 +774,7 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
                 const float* pl_ = ph_ + g.ncell;
                 const float gp =
                     __fadd_rn(__fsub_rn(ph_[idx], ph_[m]), __fsub_rn(pl_[idx], pl_[m])) * tau_h;
-                ov[d][idx] = T(float(sv[d][idx]) - beta * gp);
+                ov[d][idx] = T(float(us) - beta * gp);
             }
         }
     });
@@ -674,7 +791,7 @@ void launch_correct(const Dims& g, const Phys& ph, const T* phi, const double* c
     const float* f1 = beta32 ? beta32[1] : nullptr;
     const float* f2 = beta32 ? beta32[DIM == 3 ? 2 : 1] : nullptr;
     if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
-        if (f0 != nullptr) {
+        if (f0 != nullptr && ph.momentum == 0) {
             launch_correct3d(g, beta32, ustar, p, tau, uout, s);
             return;
         }
@@ -824,7 +941,8 @@ void launch_sub_mean(double* x, int n, const double* sum_ptr, double inv_n, cuda
     template void launch_gamma<T, D>(const Dims&, const T* const*, double, double, double*,     \
                                      RedBuf, cudaStream_t);                                     \
     template void launch_divergence<T, D>(const Dims&, const T* const*, double, double*,        \
-                                          RedBuf, CGScalars*, cudaStream_t);                    \
+                                          RedBuf, CGScalars*, cudaStream_t, const T*,           \
+                                          const Phys*);                                         \
     template void launch_correct<T, D>(const Dims&, const Phys&, const T*, const double* const*, \
                                        const float* const*, const T* const*, const double*,     \
                                        double, T* const*, cudaStream_t);                        \

@@ -160,3 +160,23 @@ def test_checkpoint_segments_cover_the_run(pf):
         assert all(b == a + c for (a, c), (b, _) in zip(segs, segs[1:]))
     with pytest.raises(ValueError):
         checkpoint_segments(5, 0)
+
+
+def test_momentum_transport_validation(pf):
+    """Consistent transport needs the CDI model (its mass flux is the CDI flux)."""
+    import pf_inputs as I
+
+    ok = pf.make_params(I.small_case(dim=2, n=32, momentum="consistent"))
+    assert pf.pf_workspace_size(ok) > 0
+    for bad in (dict(momentum="consistent", model="sb"), dict(momentum="consistent", model="isodi")):
+        q = pf.make_params(I.small_case(dim=2, n=32, **bad))
+        with pytest.raises(pf.PFError) as e:
+            pf.pf_workspace_size(q)
+        assert e.value.status == pf.B.PF_ERR_INVALID
+    q = pf.make_params(I.small_case(dim=2, n=32))
+    q.momentum = 2
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(q)
+    q = pf.make_params(I.small_case(dim=2, n=32, momentum="consistent"))
+    with pytest.raises(pf.PFError):
+        pf.B.pf_adjoint_workspace_size(q)

@@ -61,6 +61,14 @@ def workload(name, n=None):
                 f"La log-uniform in [1e2, 1e5], rho ratio in {{1, 10, 1000}}, "
                 f"static or mode-2, {prec}, {cells} cells in total")
         return plist, desc
+    elif name == "osc384_consistent":
+        p = dict(I.oscillating_drop_384(precision="mixed", n=n or 384), momentum="consistent")
+        desc = (f"3D mode-2 oscillating drop {p['n'][0]}^3, rho ratio 10, CDI + EB, mixed, "
+                "consistent (conservative) momentum transport")
+    elif name == "drop256_consistent":
+        p = dict(I.static_drop_256_r1000(precision="mixed"), momentum="consistent")
+        desc = ("2D static drop 256^2, rho ratio 1000, mu ratio 100, CDI + EB, mixed, "
+                "consistent (conservative) momentum transport")
     elif name == "drop64":
         p = I.static_drop_64()
         desc = "2D static drop 64^2, FP64, CDI + EB, La = 12000"

@@ -739,6 +739,7 @@ struct ImplT final : Impl {
     // such call runs inside the capture).
     pf_status capture_step() {
         sweep3d_prepare();
+        coarse_prepare();
         // the legacy default stream cannot be captured: record on a private
         // stream (recording runs nothing); the graph replays on the context's
         cudaStream_t own = st, rec = nullptr;

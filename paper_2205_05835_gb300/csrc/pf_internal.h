@@ -146,6 +146,8 @@ bool sweep3d_ok(const Dims& g);
 // Sets the sweep kernels' launch attributes (done by the first launch
 // otherwise); called before a stream capture.
 void sweep3d_prepare();
+// Same for the shared-memory coarse-grid kernels.
+void coarse_prepare();
 long long sweep3d_blocks(const Dims& g);   // CTAs of a tiled sweep / direction kernel
 // dots: also form r.z (r = the level's f, z = x_out) and z.q and set the CG
 // beta / rz scalars (the work of the CG dot kernel), first: no previous q.

@@ -19,6 +19,8 @@
 // smoother, correction), and each inner solve reduces its residual by eta.
 #include <type_traits>
 
+#include <mutex>
+
 #include "pf_device.cuh"
 
 namespace pf {
@@ -279,11 +281,13 @@ template void launch_beta0_32<3>(const Dims&, const Phys&, const float*, float* 
 // single-CTA kernel for all levels >= first_coarse
 // ---------------------------------------------------------------------------
 constexpr int kCoarseThreads = 1024;
+constexpr size_t kCoarseSmemMax = 200 * 1024;   // staged coarse hierarchy, bytes
 
 template <typename T, int DIM>
 __device__ __forceinline__ void cta_cells(const Dims& g, int color, bool all, const MGLevel<T>& L,
-                                          const T* phi, const Phys& ph, bool zero_start) {
-    for (int idx = threadIdx.x; idx < g.ncell; idx += blockDim.x) {
+                                          const T* phi, const Phys& ph, bool zero_start,
+                                          int t0, int nt) {
+    for (int idx = t0; idx < g.ncell; idx += nt) {
         Cell c = decode(idx, g);
         const bool act = ((c.i + c.j + c.k) & 1) == color;
         if (act) gs_cell<T, DIM>(L, phi, ph, c.i, c.j, c.k, idx, zero_start);
@@ -291,23 +295,25 @@ __device__ __forceinline__ void cta_cells(const Dims& g, int color, bool all, co
     }
 }
 
+// V-cycle over levels l0..lb of L (one CTA): pre-sweeps and restriction on the
+// way down, many sweeps on the coarsest level (after removing the mean of its
+// right-hand side), prolongation and post-sweeps on the way up.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kCoarseThreads)
-k_coarse_vcycle(MGHier<T> H, const T* __restrict__ phi, Phys ph, const CGScalars* sc) {
-    if (inner_stopped(sc)) return;
-    __shared__ double red[32];
+__device__ __forceinline__ void coarse_vcycle_body(MGLevel<T>* L_, int l0, int lb, int pre,
+                                                   int post, int coarse_sweeps,
+                                                   const T* __restrict__ phi, const Phys& ph,
+                                                   double* red) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int l0 = H.first_coarse, lb = H.nlev - 1;
     // down
     for (int l = l0; l < lb; ++l) {
-        const MGLevel<T>& L = H.lev[l];
-        for (int s = 0; s < H.pre; ++s) {
-            cta_cells<T, DIM>(L.g, 0, s == 0, L, phi, ph, s == 0);
+        const MGLevel<T>& L = L_[l];
+        for (int s = 0; s < pre; ++s) {
+            cta_cells<T, DIM>(L.g, 0, s == 0, L, phi, ph, s == 0, tid, nt);
             __syncthreads();
-            cta_cells<T, DIM>(L.g, 1, false, L, phi, ph, false);
+            cta_cells<T, DIM>(L.g, 1, false, L, phi, ph, false, tid, nt);
             __syncthreads();
         }
-        const MGLevel<T>& C = H.lev[l + 1];
+        const MGLevel<T>& C = L_[l + 1];
         for (int I = tid; I < C.g.ncell; I += nt) {
             Cell c = decode(I, C.g);
             restrict_cell<T, DIM>(L, C, phi, ph, c.i, c.j, c.k, I);
@@ -316,7 +322,7 @@ k_coarse_vcycle(MGHier<T> H, const T* __restrict__ phi, Phys ph, const CGScalars
     }
     // bottom: remove the mean of f (compatibility), then many sweeps
     {
-        const MGLevel<T>& L = H.lev[lb];
+        const MGLevel<T>& L = L_[lb];
         double s = 0.0;
         for (int i = tid; i < L.g.ncell; i += nt) s += double(L.f[i]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -331,28 +337,105 @@ k_coarse_vcycle(MGHier<T> H, const T* __restrict__ phi, Phys ph, const CGScalars
         const T mean = T(red[0]);
         for (int i = tid; i < L.g.ncell; i += nt) L.f[i] -= mean;
         __syncthreads();
-        for (int s2 = 0; s2 < H.coarse_sweeps; ++s2) {
-            cta_cells<T, DIM>(L.g, 0, s2 == 0, L, phi, ph, s2 == 0);
+        for (int s2 = 0; s2 < coarse_sweeps; ++s2) {
+            cta_cells<T, DIM>(L.g, 0, s2 == 0, L, phi, ph, s2 == 0, tid, nt);
             __syncthreads();
-            cta_cells<T, DIM>(L.g, 1, false, L, phi, ph, false);
+            cta_cells<T, DIM>(L.g, 1, false, L, phi, ph, false, tid, nt);
             __syncthreads();
         }
     }
     // up
     for (int l = lb - 1; l >= l0; --l) {
-        const MGLevel<T>& L = H.lev[l];
+        const MGLevel<T>& L = L_[l];
         for (int i = tid; i < L.g.ncell; i += nt) {
             Cell c = decode(i, L.g);
-            prolong_cell<T, DIM>(L, H.lev[l + 1], c.i, c.j, c.k, i);
+            prolong_cell<T, DIM>(L, L_[l + 1], c.i, c.j, c.k, i);
         }
         __syncthreads();
-        for (int s = 0; s < H.post; ++s) {
-            cta_cells<T, DIM>(L.g, 1, false, L, phi, ph, false);
+        for (int s = 0; s < post; ++s) {
+            cta_cells<T, DIM>(L.g, 1, false, L, phi, ph, false, tid, nt);
             __syncthreads();
-            cta_cells<T, DIM>(L.g, 0, false, L, phi, ph, false);
+            cta_cells<T, DIM>(L.g, 0, false, L, phi, ph, false, tid, nt);
             __syncthreads();
         }
     }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kCoarseThreads)
+k_coarse_vcycle(MGHier<T> H, const T* __restrict__ phi, Phys ph, const CGScalars* sc) {
+    if (inner_stopped(sc)) return;
+    __shared__ double red[32];
+    __shared__ MGLevel<T> Ls[kMaxLevels];   // one copy of the level descriptors
+    if (threadIdx.x == 0)
+        for (int l = 0; l < H.nlev; ++l) Ls[l] = H.lev[l];
+    __syncthreads();
+    coarse_vcycle_body<T, DIM>(Ls, H.first_coarse, H.nlev - 1, H.pre, H.post, H.coarse_sweeps,
+                               phi, ph, red);
+}
+
+// The same V-cycle on copies in shared memory: every coarse level's
+// correction, right-hand side and face coefficients (about 85 KB for a 2D
+// float32 hierarchy below 64^2) are staged in once, so the ~70 dependent
+// half-sweeps and transfers of one call run at shared-memory latency instead
+// of L2 latency. Only the first coarse level's right-hand side (written by
+// the restriction) comes in and only its correction goes out.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kCoarseThreads)
+k_coarse_vcycle_smem(MGHier<T> H, const T* __restrict__ phi, Phys ph, const CGScalars* sc) {
+    if (inner_stopped(sc)) return;
+    __shared__ double red[32];
+    extern __shared__ __align__(16) unsigned char craw[];
+    T* sm = reinterpret_cast<T*>(craw);
+    const int l0 = H.first_coarse, lb = H.nlev - 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ MGLevel<T> S[kMaxLevels];   // level descriptors viewing the staged copies
+    if (tid == 0) {
+        int off = 0;
+        for (int l = l0; l <= lb; ++l) {
+            S[l] = H.lev[l];
+            const int n = S[l].g.ncell;
+            S[l].x = sm + off;
+            off += n;
+            S[l].f = sm + off;
+            off += n;
+            for (int d = 0; d < 3; ++d) {
+                S[l].beta[d] = d < DIM ? sm + off : nullptr;
+                if (d < DIM) off += n;
+            }
+        }
+    }
+    __syncthreads();
+    for (int l = l0; l <= lb; ++l)
+        for (int d = 0; d < DIM; ++d)
+            for (int i = tid; i < S[l].g.ncell; i += nt) S[l].beta[d][i] = H.lev[l].beta[d][i];
+    for (int i = tid; i < S[l0].g.ncell; i += nt) S[l0].f[i] = H.lev[l0].f[i];
+    __syncthreads();
+    coarse_vcycle_body<T, DIM>(S, l0, lb, H.pre, H.post, H.coarse_sweeps, phi, ph, red);
+    for (int i = tid; i < S[l0].g.ncell; i += nt) H.lev[l0].x[i] = S[l0].x[i];
+}
+
+// shared-memory bytes of the staged coarse hierarchy, or 0 when it does not
+// fit (or a level computes its coefficients from phi)
+template <typename T, int DIM>
+size_t coarse_smem_bytes(const MGHier<T>& H) {
+    size_t n = 0;
+    for (int l = H.first_coarse; l < H.nlev; ++l) {
+        for (int d = 0; d < DIM; ++d)
+            if (H.lev[l].beta[d] == nullptr) return 0;
+        n += (size_t)H.lev[l].g.ncell * (2 + DIM);
+    }
+    const size_t bytes = n * sizeof(T);
+    return bytes <= kCoarseSmemMax ? bytes : 0;
+}
+
+template <typename T, int DIM>
+void coarse_smem_attribute() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_coarse_vcycle_smem<T, DIM>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
+    });
 }
 
 template <typename T, int DIM>
@@ -439,7 +522,13 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
         pr->end();
     }
     pr->begin(KC_COARSE);
-    k_coarse_vcycle<T, DIM><<<1, kCoarseThreads, 0, s>>>(H, phi, ph, sc);
+    const size_t cbytes = coarse_smem_bytes<T, DIM>(H);
+    if (cbytes > 0) {
+        coarse_smem_attribute<T, DIM>();
+        k_coarse_vcycle_smem<T, DIM><<<1, kCoarseThreads, cbytes, s>>>(H, phi, ph, sc);
+    } else {
+        k_coarse_vcycle<T, DIM><<<1, kCoarseThreads, 0, s>>>(H, phi, ph, sc);
+    }
     pr->end();
     for (int l = l0 - 1; l >= 0; --l) {
         MGLevel<T> L = H.lev[l];
@@ -776,6 +865,13 @@ k_in_update(Dims g, SolveIO<T, DIM> io, int cur, int first_arg, RedBuf rb, CGSca
             sc->capped = 1;
         }
     }
+}
+
+void coarse_prepare() {
+    coarse_smem_attribute<float, 2>();
+    coarse_smem_attribute<float, 3>();
+    coarse_smem_attribute<double, 2>();
+    coarse_smem_attribute<double, 3>();
 }
 
 // Condition of a WHILE node of a solve captured in a CUDA graph: which = 0

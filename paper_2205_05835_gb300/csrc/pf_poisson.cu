@@ -283,15 +283,32 @@ template void launch_beta0_32<3>(const Dims&, const Phys&, const float*, float* 
 constexpr int kCoarseThreads = 1024;
 constexpr size_t kCoarseSmemMax = 200 * 1024;   // staged coarse hierarchy, bytes
 
+// One colour of a red-black sweep over a (small) level by threads t0, t0 + nt,
+// ...: item q = (row, m) with cell i = 2 m + parity(row) of the colour; all:
+// the other colour's cell of the pair is zeroed. Rows and positions come from
+// float reciprocals (exact: q < 2^12 on the levels this runs on, so q + 1/2
+// stays far from a multiple of the divisor after rounding).
 template <typename T, int DIM>
 __device__ __forceinline__ void cta_cells(const Dims& g, int color, bool all, const MGLevel<T>& L,
                                           const T* phi, const Phys& ph, bool zero_start,
                                           int t0, int nt) {
-    for (int idx = t0; idx < g.ncell; idx += nt) {
-        Cell c = decode(idx, g);
-        const bool act = ((c.i + c.j + c.k) & 1) == color;
-        if (act) gs_cell<T, DIM>(L, phi, ph, c.i, c.j, c.k, idx, zero_start);
-        else if (all) L.x[idx] = T(0);
+    const int nhx = (g.nx + 1) >> 1;
+    const int rows = g.ny * g.nz;
+    const int items = rows * nhx;
+    const float inv_nhx = 1.0f / float(nhx), inv_ny = 1.0f / float(g.ny);
+    for (int q = t0; q < items; q += nt) {
+        const int r = int((float(q) + 0.5f) * inv_nhx);
+        const int m = q - r * nhx;
+        const int k = int((float(r) + 0.5f) * inv_ny);
+        const int j = r - k * g.ny;
+        const int par = (j + k + color) & 1;
+        const int i = 2 * m + par;
+        const int base = r * g.nx;
+        if (i < g.nx) gs_cell<T, DIM>(L, phi, ph, i, j, k, base + i, zero_start);
+        if (all) {
+            const int io = 2 * m + (1 - par);
+            if (io < g.nx) L.x[base + io] = T(0);
+        }
     }
 }
 

@@ -312,6 +312,17 @@ __device__ __forceinline__ void cta_cells(const Dims& g, int color, bool all, co
     }
 }
 
+// Cell coordinates of a linear index on a small level by float reciprocals
+// (exact for idx < 2^12: idx + 1/2 stays far from a multiple of nx or ny).
+__device__ __forceinline__ Cell decode_small(int idx, const Dims& g, float inv_nx, float inv_ny) {
+    Cell c;
+    const int r = int((float(idx) + 0.5f) * inv_nx);
+    c.i = idx - r * g.nx;
+    c.k = int((float(r) + 0.5f) * inv_ny);
+    c.j = r - c.k * g.ny;
+    return c;
+}
+
 // V-cycle over levels l0..lb of L (one CTA): pre-sweeps and restriction on the
 // way down, many sweeps on the coarsest level (after removing the mean of its
 // right-hand side), prolongation and post-sweeps on the way up.
@@ -331,8 +342,9 @@ __device__ __forceinline__ void coarse_vcycle_body(MGLevel<T>* L_, int l0, int l
             __syncthreads();
         }
         const MGLevel<T>& C = L_[l + 1];
+        const float cix = 1.0f / float(C.g.nx), ciy = 1.0f / float(C.g.ny);
         for (int I = tid; I < C.g.ncell; I += nt) {
-            Cell c = decode(I, C.g);
+            Cell c = decode_small(I, C.g, cix, ciy);
             restrict_cell<T, DIM>(L, C, phi, ph, c.i, c.j, c.k, I);
         }
         __syncthreads();
@@ -364,8 +376,9 @@ __device__ __forceinline__ void coarse_vcycle_body(MGLevel<T>* L_, int l0, int l
     // up
     for (int l = lb - 1; l >= l0; --l) {
         const MGLevel<T>& L = L_[l];
+        const float fix = 1.0f / float(L.g.nx), fiy = 1.0f / float(L.g.ny);
         for (int i = tid; i < L.g.ncell; i += nt) {
-            Cell c = decode(i, L.g);
+            Cell c = decode_small(i, L.g, fix, fiy);
             prolong_cell<T, DIM>(L, L_[l + 1], c.i, c.j, c.k, i);
         }
         __syncthreads();

@@ -20,6 +20,14 @@ table to compare with the figure's trends (EB second order), not a parity
 check.
 
     python -m paper_2205_05835_gb300.studies --panel h --tstar 250
+
+A second driver compares the forces and the precisions on the density-ratio-
+1000 static drop (256^2, rho 240 / 0.24, mu 0.1 / 0.001, CDI, eps = dx):
+EB, CSF and LCSF each in float64 and in mixed precision, run concurrently,
+reporting the spurious currents, the Laplace pressure jump against sigma / R
+and the mixed path's per-field distance from the float64 run of the same force:
+
+    python -m paper_2205_05835_gb300.studies --compare --steps 2000
 """
 from __future__ import annotations
 
@@ -95,6 +103,58 @@ def convergence_study(panel="h", ns=(32, 64, 128, 256), models=("cdi", "sb", "is
             "steps": {f"{m}-{f}-{n}": s for (m, f, n), s in zip(keys, steps)}}
 
 
+def force_precision_comparison(n=256, steps=2000, forces=("eb", "csf", "lcsf"),
+                               use_graph=1):
+    """The static drop at density ratio 1000 for every force in float64 and
+    mixed precision (one batch); per force: Ca_inf, Laplace jump dp and its
+    relative deviation from sigma / R in both precisions (after the first step,
+    the pressure balancing the initial equilibrium profile, and at the end),
+    and the max-norm relative distance of the mixed fields from the float64
+    fields."""
+    import numpy as np
+
+    import paper_2205_05835_gb300 as pf
+    import pf_inputs as I
+
+    plist, keys = [], []
+    for f in forces:
+        for prec in ("fp64", "mixed"):
+            p = I.static_drop_256_r1000(force=f, precision=prec)
+            p["n"] = (n, n, 1)
+            p["eps"] = None
+            p["dt"] = None
+            p = I.finalize(p)
+            p["use_graph"] = use_graph
+            plist.append(p)
+            keys.append((f, prec))
+    bat = pf.Batch(plist)
+    t0 = time.perf_counter()
+    bat.step(1)
+    dp1 = [bat.diagnostics(i)["dp_laplace"] for i in range(len(plist))]
+    bat.step(steps - 1)
+    wall = time.perf_counter() - t0
+    out = {"n": n, "steps": steps, "wall_s": wall, "forces": {}}
+    for f in forces:
+        i64, i32 = keys.index((f, "fp64")), keys.index((f, "mixed"))
+        row = {}
+        for prec, i in (("fp64", i64), ("mixed", i32)):
+            d = bat.diagnostics(i)
+            ref = plist[i]["sigma"] / plist[i]["R"]
+            row[prec] = {"ca_inf": d["ca_inf"], "dp": d["dp_laplace"],
+                         "dp_rel_to_sigma_over_R": d["dp_laplace"] / ref - 1.0,
+                         "dp_first_step_rel": dp1[i] / ref - 1.0,
+                         "mass": d["mass"], "phi_min": d["phi_min"], "phi_max": d["phi_max"],
+                         "t": d["t"]}
+        errs = {}
+        for name in ("phi", "u", "v", "p"):
+            a, b = bat.field(i64, name), bat.field(i32, name)
+            errs[name] = float(np.max(np.abs(b - a)) / max(float(np.max(np.abs(a))), 1e-300))
+        row["mixed_vs_fp64"] = errs
+        out["forces"][f] = row
+    bat.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--panel", choices=("h", "eps"), default="h")
@@ -104,7 +164,14 @@ def main():
     ap.add_argument("--forces", type=str, default="eb,csf,lcsf")
     ap.add_argument("--precision", type=str, default="mixed")
     ap.add_argument("--threads", type=int, default=16)
+    ap.add_argument("--compare", action="store_true",
+                    help="forces x precisions on the density-ratio-1000 drop")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=2000)
     args = ap.parse_args()
+    if args.compare:
+        print(json.dumps(force_precision_comparison(n=args.n, steps=args.steps)))
+        return
     res = convergence_study(panel=args.panel, ns=tuple(int(v) for v in args.ns.split(",")),
                             models=tuple(args.models.split(",")),
                             forces=tuple(args.forces.split(",")), tstar=args.tstar,

@@ -63,6 +63,7 @@ enum { PF_FORCE_EB = 0, PF_FORCE_CSF = 1, PF_FORCE_LCSF = 2 }; /* surface tensio
 enum { PF_FP64 = 0, PF_MIXED = 1 };                         /* precision of stencils and V-cycles */
 enum { PF_RK4_PROJ = 0, PF_FE = 1 };                        /* time integrator */
 enum { PF_MOMENTUM_ADVECTIVE = 0, PF_MOMENTUM_CONSISTENT = 1 }; /* momentum transport */
+enum { PF_SHAPE_DROP = 0, PF_SHAPE_WAVE = 1 };              /* initial phi (pf_params.shape) */
 enum { PF_FIELD_PHI = 0, PF_FIELD_U = 1, PF_FIELD_V = 2, PF_FIELD_W = 3, PF_FIELD_P = 4 };
 
 typedef struct {
@@ -105,7 +106,17 @@ typedef struct {
                              with the phase-field flux (the transport the paper's Section 3
                              takes from its reference Mirjalili 2021; the discrete form is this
                              library's). Stage velocities are the new momentum over rho_f. */
-    int reserved[6];      /* must be zero */
+    int wall_y;           /* 0: periodic in y. 1 (2D, advective momentum): free-slip walls at
+                             y = 0 and y = n[1] dx (Section 3.2 standing wave): zero normal
+                             velocity, no flux of phi and a homogeneous Neumann condition on p
+                             at the walls; phi, the x-velocity and every other cell-centred
+                             quantity mirror across them (zero normal gradient). The y-face of
+                             index 0 is the wall (face n[1] wraps to it); it holds v = 0. */
+    int shape;            /* initial phi when pf_init gets no phi0: PF_SHAPE_DROP, or
+                             PF_SHAPE_WAVE (needs wall_y = 1): phi = 1 below the interface
+                             y = R (1 - pert_amp cos(k (x - dx/2))), k = 2 pi pert_mode / (n[0] dx)
+                             (R: mean height, pert_amp: amplitude over R) */
+    int reserved[4];      /* must be zero */
 } pf_params;
 
 typedef struct {
@@ -258,7 +269,8 @@ const char* pf_batch_last_error(const pf_batch* b);
  * pf_adjoint_workspace_size: bytes of the adjoint workspace (device memory,
  * 256-byte aligned, caller-owned) that pf_step_adjoint needs for these
  * parameters (54 doubles per cell in 2D, 74 in 3D). PF_ERR_INVALID for
- * unsupported parameters (mixed precision, SB / ISODI, CSF / LCSF).
+ * unsupported parameters (mixed precision, SB / ISODI, CSF / LCSF, consistent
+ * momentum transport, walls in y).
  *
  * pf_step_adjoint: transposed Jacobian of one step applied to a cotangent.
  *  state_n: the state at the start of the step in the pf_get_state layout

@@ -21,7 +21,9 @@ readings below are this implementation's):
     velocity component d lives on the d-faces, and face i - 1/2 is stored at
     index i (between cells i - 1 and i);
   * central second-order differences everywhere; projected RK4 or forward
-    Euler in time.
+    Euler in time;
+  * optionally free-slip walls at y = 0 and y = ny h instead of periodicity in
+    y (the standing wave of Section 3.2), imposed through image rows.
 
 Parity status: every function below is pinned by tests/test_oracle_pins.py
 against closed forms, invariants, brute-force matrices or exact solutions,
@@ -45,6 +47,8 @@ _MODELS = {"cdi": 0, "sb": 1, "isodi": 2}
 _FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 _SCHEMES = {"rk4": 0, "fe": 1}
 _MOMENTUM = {"advective": 0, "consistent": 1}
+_SHAPES = {"drop": 0, "wave": 1}
+SHAPE_DROP, SHAPE_WAVE = 0, 1
 
 # Projected RK4 (classical tableau): stage time fractions and weights.
 RK4_C = (0.0, 0.5, 0.5, 1.0)
@@ -89,7 +93,7 @@ def params_from(p):
     """Normalise a parameter dict (names from pf_inputs) to oracle form."""
     q = dict(p)
     for key, table in (("model", _MODELS), ("force", _FORCES), ("scheme", _SCHEMES),
-                       ("momentum", _MOMENTUM)):
+                       ("momentum", _MOMENTUM), ("shape", _SHAPES)):
         if isinstance(q.get(key), str):
             q[key] = table[q[key]]
     return q
@@ -105,9 +109,18 @@ def initial_phi(p):
     The drop is centred in the box (at n_d h / 2 along each axis). Its radius is R(theta) = R (1 + a cos(n
     theta)) in 2D and R (1 + a P_n(cos theta)) in 3D (theta measured from the z
     axis); R(theta) - r is taken as the signed distance for a perturbed drop.
+
+    Standing wave (shape 1, Section 3.2, 2D): the interface height is
+    y0 - A0 cos(k (x - dx/2)) with y0 = R and A0 = a R, k = 2 pi n / (nx h) (n
+    wavelengths across the box); y_i(x) - y is the signed distance, phi = 1
+    below the interface.
     """
     g = Grid(p["dim"], p["n"], p["L"])
     X = g.centres()
+    if p.get("shape", SHAPE_DROP) == SHAPE_WAVE:
+        k = 2.0 * math.pi * int(p["pert_mode"]) / (g.n[0] * g.h)
+        yi = p["R"] * (1.0 - float(p["pert_amp"]) * np.cos(k * (X[0] - 0.5 * g.h)))
+        return 0.5 * (1.0 + np.tanh((yi - X[1]) / (2.0 * p["eps"])))
     rel = [X[d] - 0.5 * g.n[d] * g.h for d in range(g.dim)]
     r = np.sqrt(sum(v * v for v in rel))
     R = p["R"]
@@ -447,19 +460,98 @@ def solve_poisson(beta, rhs, g):
     return x.reshape(g.shape)
 
 
+def pressure_beta(phi, g, p):
+    """Face coefficients of the projection: 1 / rho_f, and 0 on the wall faces
+    when walls bound the box in y (no flux through a wall: the homogeneous
+    Neumann condition of the pressure there)."""
+    beta = face_beta(phi, g, p)
+    if p.get("wall_y", 0):
+        beta[1] = beta[1].copy()
+        _wall_rows(beta[1], g)[...] = 0.0
+    return beta
+
+
 def project(ustar, phi, g, p, tau):
     """u = u* - tau beta G p with D(beta G p) = D u* / tau, mean(p) = 0.
 
     The pressure solves A p = -b, A = -D beta G, b = D u* / tau projected to
-    zero mean; p is the physical pressure of the stage.
+    zero mean; p is the physical pressure of the stage. Between walls in y the
+    wall faces carry beta = 0, so p obeys dp/dn = 0 there and the wall's
+    normal velocity (zero in u*) is not corrected.
     """
-    beta = face_beta(phi, g, p)
+    beta = pressure_beta(phi, g, p)
     b = divergence(ustar, g) / tau
     b = b - b.mean()
     pr = solve_poisson(beta, -b, g)
     Gp = gradient_faces(pr, g)
     u = [ustar[d] - tau * beta[d] * Gp[d] for d in range(g.dim)]
     return u, pr
+
+
+# ----------------------------------------------------------------------------
+# free-slip walls in y (Section 3.2 standing wave: periodic in x, free slip on
+# the top and bottom walls)
+# ----------------------------------------------------------------------------
+# The walls lie at y = 0 and y = ny h, on the y-face of index 0 (face ny wraps
+# to it). Free slip: zero normal velocity and zero tangential stress; with no
+# flux of phi through a wall and phi of zero normal gradient there. The
+# right-hand sides are evaluated on the box extended by WALL_GHOST image rows
+# beyond each wall: cell-centred quantities (phi, the x-velocity) mirror
+# (cell -1-j is cell j), the y-velocity is odd about the wall faces
+# (v(-j) = -v(j), v(ny) = 0). Every stencil then sees a zero normal gradient
+# of phi, a zero normal velocity and a zero shear du/dy at the walls; normals,
+# chemical potential and curvature computed from the images carry the right
+# parity by construction. Stencils reach at most three cells.
+WALL_GHOST = 3
+
+
+def _wall_rows(a, g):
+    """View of the y-face row 0 (the wall faces) of a face array."""
+    return np.moveaxis(a, g.axis(1), 0)[0]
+
+
+def _pad_y(a, g, odd_face):
+    """a extended by WALL_GHOST image rows below y = 0 and above y = ny h."""
+    G = WALL_GHOST
+    b = np.moveaxis(a, g.axis(1), 0)
+    ny = b.shape[0]
+    if odd_face:
+        lo = -b[G:0:-1]                                                   # faces -G .. -1
+        hi = np.concatenate([np.zeros_like(b[:1]), -b[ny - 1:ny - G:-1]])  # faces ny .. ny+G-1
+    else:
+        lo = b[G - 1::-1]                                                 # cells -G .. -1
+        hi = b[ny - 1:ny - 1 - G:-1]                                      # cells ny .. ny+G-1
+    return np.moveaxis(np.concatenate([lo, b, hi]), 0, g.axis(1))
+
+
+def _crop_y(a, g):
+    """The rows of the box proper from an array on the extended box."""
+    b = np.moveaxis(a, g.axis(1), 0)
+    return np.moveaxis(b[WALL_GHOST:b.shape[0] - WALL_GHOST], 0, g.axis(1))
+
+
+def _extended(phi, u, g):
+    n = list(g.n)
+    n[1] += 2 * WALL_GHOST
+    ge = Grid(g.dim, n, g.L)
+    ue = [_pad_y(u[d], g, odd_face=(d == 1)) for d in range(g.dim)]
+    return ge, _pad_y(phi, g, False), ue
+
+
+def phase_rhs_walls(phi, u, g, p, gamma):
+    """phase_rhs between free-slip walls in y (image rows beyond the walls)."""
+    ge, phie, ue = _extended(phi, u, g)
+    return _crop_y(phase_rhs(phie, ue, ge, p, gamma), g)
+
+
+def momentum_rhs_walls(phi, u, g, p):
+    """momentum_rhs between free-slip walls in y; the wall's normal velocity
+    has no right-hand side (it stays zero)."""
+    ge, phie, ue = _extended(phi, u, g)
+    k = [_crop_y(c, g) for c in momentum_rhs(phie, ue, ge, p)]
+    k[1] = k[1].copy()
+    _wall_rows(k[1], g)[...] = 0.0
+    return k
 
 
 # ----------------------------------------------------------------------------
@@ -505,6 +597,13 @@ def step(st, p):
     gam = gamma_of(st.u, p)
     phin, un = st.phi, st.u
     cons = p.get("momentum", MOMENTUM_ADVECTIVE) == MOMENTUM_CONSISTENT
+    walls = bool(p.get("wall_y", 0))
+    if walls and (cons or g.dim != 2):
+        raise ValueError("walls in y: 2D with advective momentum transport")
+
+    def prhs(ph, uu):
+        return phase_rhs_walls(ph, uu, g, p, gam) if walls else phase_rhs(ph, uu, g, p, gam)
+
     if cons:
         # consistent transport advances rho_f u: the stage velocity is the new
         # momentum divided by the face density of the new phase field
@@ -521,12 +620,12 @@ def step(st, p):
         vn = un
 
         def krhs(ph, uu):
-            return momentum_rhs(ph, uu, g, p)
+            return momentum_rhs_walls(ph, uu, g, p) if walls else momentum_rhs(ph, uu, g, p)
 
         def vel(v, ph):
             return v
     if p["scheme"] == SCHEME_FE:
-        kphi = phase_rhs(phin, un, g, p, gam)
+        kphi = prhs(phin, un)
         ku = krhs(phin, un)
         phi1 = phin + dt * kphi
         ustar = vel([vn[d] + dt * ku[d] for d in range(g.dim)], phi1)
@@ -537,7 +636,7 @@ def step(st, p):
     acc_u = None
     pr = st.p
     for s in range(4):
-        kphi = phase_rhs(phis, us, g, p, gam)
+        kphi = prhs(phis, us)
         ku = krhs(phis, us)
         wdt = RK4_W[s] * dt
         if s < 3:
@@ -569,7 +668,7 @@ def run(p, steps=None, phi0=None, record=False):
 # ----------------------------------------------------------------------------
 # diagnostics (Section 3.1 Ca_inf, Section 3.2 energies)
 # ----------------------------------------------------------------------------
-def surface_energy(phi, g, sigma, eps):
+def surface_energy(phi, g, sigma, eps, wall_y=0):
     """SE = sum [ (sigma_hat/eps) psi + (sigma_hat eps / 2) |grad phi|^2 ] dV.
 
     |grad phi|^2 is the sum of squared face differences, so d SE / d phi_i / dV
@@ -578,7 +677,10 @@ def surface_energy(phi, g, sigma, eps):
     in Section 3.2 omits it (reading: a misprint).
     """
     sh = 6.0 * sigma
-    grad2 = sum(face_diff(phi, g, d) ** 2 for d in range(g.dim))
+    terms = [face_diff(phi, g, d) ** 2 for d in range(g.dim)]
+    if wall_y:
+        _wall_rows(terms[1], g)[...] = 0.0    # phi mirrors across a wall: no jump there
+    grad2 = sum(terms)
     return float(np.sum((sh / eps) * psi(phi) + 0.5 * sh * eps * grad2) * g.dV)
 
 
@@ -594,7 +696,7 @@ def diagnostics(st, p):
     inside, outside = phi >= 0.999, phi <= 0.001
     dp = float(pr[inside].mean() - pr[outside].mean()) if inside.any() and outside.any() else 0.0
     return dict(mass=float(np.sum(phi)) * g.dV, ke=ke,
-                se=surface_energy(phi, g, p["sigma"], p["eps"]),
+                se=surface_energy(phi, g, p["sigma"], p["eps"], p.get("wall_y", 0)),
                 umax=umax, ca_inf=umax * p["mu_in"] / p["sigma"], dp_laplace=dp,
                 phi_min=float(phi.min()), phi_max=float(phi.max()), step=st.step, t=st.t)
 

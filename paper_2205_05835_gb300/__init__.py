@@ -24,6 +24,7 @@ FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 SCHEMES = {"rk4": 0, "fe": 1}
 MOMENTUM = {"advective": 0, "consistent": 1}
+SHAPES = {"drop": 0, "wave": 1}
 FIELDS = {"phi": B.PF_FIELD_PHI, "u": B.PF_FIELD_U, "v": B.PF_FIELD_V, "w": B.PF_FIELD_W,
           "p": B.PF_FIELD_P}
 
@@ -46,10 +47,11 @@ def make_params(p: dict) -> B.pf_params:
     q.precision = enum("precision", PRECISIONS)
     q.scheme = enum("scheme", SCHEMES)
     q.momentum = enum("momentum", MOMENTUM)
+    q.shape = enum("shape", SHAPES)
     for k in ("sigma", "eps", "rho_in", "rho_out", "mu_in", "mu_out", "gamma_fixed", "gamma_min",
               "dt", "delta_n", "poisson_rtol", "R", "pert_amp", "bound_tol", "inner_tol"):
         setattr(q, k, float(p.get(k, 0.0) or 0.0))
-    for k in ("poisson_maxit", "pert_mode", "mg_pre", "mg_post", "use_graph"):
+    for k in ("poisson_maxit", "pert_mode", "mg_pre", "mg_post", "use_graph", "wall_y"):
         setattr(q, k, int(p.get(k, 0) or 0))
     return q
 

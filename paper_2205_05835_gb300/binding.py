@@ -49,7 +49,9 @@ class pf_params(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("use_graph", ctypes.c_int),
         ("momentum", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("wall_y", ctypes.c_int),
+        ("shape", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 

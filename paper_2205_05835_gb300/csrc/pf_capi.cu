@@ -183,7 +183,20 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "consistent momentum transport needs the CDI model";
         return PF_ERR_INVALID;
     }
-    for (int i = 0; i < 6; ++i)
+    if (p->wall_y != 0 && p->wall_y != 1) { why = "wall_y must be 0 or 1"; return PF_ERR_INVALID; }
+    if (p->wall_y == 1 && (p->dim != 2 || p->momentum != PF_MOMENTUM_ADVECTIVE)) {
+        why = "walls in y need dim 2 and advective momentum transport";
+        return PF_ERR_INVALID;
+    }
+    if (p->shape != PF_SHAPE_DROP && p->shape != PF_SHAPE_WAVE) {
+        why = "bad initial shape";
+        return PF_ERR_INVALID;
+    }
+    if (p->shape == PF_SHAPE_WAVE && p->wall_y != 1) {
+        why = "the standing-wave shape needs walls in y";
+        return PF_ERR_INVALID;
+    }
+    for (int i = 0; i < 4; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
     return PF_OK;
 }
@@ -248,6 +261,7 @@ struct ImplT final : Impl {
     ImplT(const pf_params& p_, cudaStream_t s_, std::string& e_) : prm(p_), st(s_), err(e_) {
         prof.st = s_;
         g = make_dims(prm.n[0], prm.n[1], DIM == 3 ? prm.n[2] : 1, prm.L / prm.n[0]);
+        g.wall_y = prm.wall_y;
         ph.dim = DIM;
         ph.model = prm.model;
         ph.force = prm.force;
@@ -278,6 +292,7 @@ struct ImplT final : Impl {
                       f.nx >= 4 && f.ny >= 4 && (DIM == 2 || f.nz >= 4);
             if (!ok) break;
             H.lev[H.nlev].g = make_dims(f.nx / 2, f.ny / 2, DIM == 3 ? f.nz / 2 : 1, f.h * 2.0);
+            H.lev[H.nlev].g.wall_y = f.wall_y;
             ++H.nlev;
         }
         for (int l = 0; l < kMaxLevels; ++l) H.lev[l].x2 = nullptr;
@@ -514,7 +529,8 @@ struct ImplT final : Impl {
             cudaMemcpyAsync(b, phi0, g.ncell * sizeof(double), cudaMemcpyDefault, st);
             launch_convert_in<T>(b, phiN, g.ncell, st);
         } else {
-            launch_init_phi<T, DIM>(g, ph, prm.R, prm.pert_mode, prm.pert_amp, phiN, st);
+            launch_init_phi<T, DIM>(g, ph, prm.R, prm.pert_mode, prm.pert_amp, prm.shape, phiN,
+                                    st);
         }
     }
 
@@ -1140,8 +1156,9 @@ struct ImplT final : Impl {
     bool adjoint_supported(std::string& why) const {
         if (sizeof(T) != sizeof(double)) { why = "the adjoint needs precision PF_FP64"; return false; }
         if (prm.model != PF_CDI || prm.force != PF_FORCE_EB ||
-            prm.momentum != PF_MOMENTUM_ADVECTIVE) {
-            why = "the adjoint supports the CDI model with the EB force and advective momentum";
+            prm.momentum != PF_MOMENTUM_ADVECTIVE || prm.wall_y != 0) {
+            why = "the adjoint supports the periodic CDI model with the EB force and advective "
+                  "momentum";
             return false;
         }
         return true;
@@ -1591,9 +1608,9 @@ pf_status pf_adjoint_workspace_size(const pf_params* prm, size_t* bytes) {
     if (s != PF_OK) { g_init_error = why; return s; }
     if (!bytes) { g_init_error = "bytes is NULL"; return PF_ERR_INVALID; }
     if (prm->precision != PF_FP64 || prm->model != PF_CDI || prm->force != PF_FORCE_EB ||
-        prm->momentum != PF_MOMENTUM_ADVECTIVE) {
-        g_init_error = "the adjoint supports precision PF_FP64 with the CDI model, the EB force and "
-                       "advective momentum";
+        prm->momentum != PF_MOMENTUM_ADVECTIVE || prm->wall_y != 0) {
+        g_init_error = "the adjoint supports precision PF_FP64 with the CDI model, the EB force, "
+                       "advective momentum and a periodic box";
         return PF_ERR_INVALID;
     }
     std::string err;

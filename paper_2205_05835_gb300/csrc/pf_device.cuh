@@ -7,6 +7,19 @@
 namespace pf {
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// mirror image of cell i across the walls at 0 and n (|i| < n): -1-i, 2n-1-i
+__device__ __forceinline__ int mirrori(int i, int n) {
+    return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
+}
+
+// Free-slip walls at y = 0 and y = ny h (Dims::wall_y): face q (0..5 = -x, +x,
+// -y, +y, -z, +z) of a cell in row j lies on a wall. The y-face of index 0 is
+// both walls (face ny wraps to it); the normal velocity there is zero, and so
+// are the flux of phi, the pressure operator's face coefficient (a homogeneous
+// Neumann condition) and the face gradient of phi.
+__device__ __forceinline__ bool wall_face(const Dims& g, int j, int q) {
+    return g.wall_y && ((q == 2 && j == 0) || (q == 3 && j == g.ny - 1));
+}
 
 // Cell coordinates of a linear index (x fastest).
 struct Cell {
@@ -23,15 +36,20 @@ __device__ __forceinline__ Cell decode(int idx, const Dims& g) {
 }
 
 // Wrapped neighbour index for offsets |o| <= 3 along each axis (n >= 4). Cells
-// at least 3 away from every periodic seam use plain offsets.
+// at least 3 away from every periodic seam use plain offsets. With walls in y
+// (Dims::wall_y) a cell-centred quantity mirrors across them (its image cell:
+// zero normal gradient, free slip of the tangential velocity), while the
+// y-velocity, which lives on the y-faces, is read through atv: the wrapped
+// face index, so face ny is the wall face 0 (zero normal velocity).
 template <int DIM>
 struct Nbr {
     int nx, ny, nz;
-    int idx, sz;
+    int idx, sz, cj;
     bool inner;
-    int im[7], jm[7], km[7];   // wrapped coordinates for offsets -3..3
+    int im[7], jm[7], km[7];   // wrapped (mirrored) coordinates for offsets -3..3
     __device__ __forceinline__ Nbr(const Cell& c, const Dims& g) : nx(g.nx), ny(g.ny), nz(g.nz) {
         sz = g.nx * g.ny;
+        cj = c.j;
         idx = (c.k * g.ny + c.j) * g.nx + c.i;
         inner = c.i >= 3 && c.i < g.nx - 3 && c.j >= 3 && c.j < g.ny - 3 &&
                 (DIM == 2 || (c.k >= 3 && c.k < g.nz - 3));
@@ -39,7 +57,7 @@ struct Nbr {
 #pragma unroll
             for (int o = -3; o <= 3; ++o) {
                 im[o + 3] = wrapi(c.i + o, g.nx);
-                jm[o + 3] = wrapi(c.j + o, g.ny);
+                jm[o + 3] = g.wall_y ? mirrori(c.j + o, g.ny) : wrapi(c.j + o, g.ny);
                 km[o + 3] = (DIM == 3) ? wrapi(c.k + o, g.nz) : 0;
             }
         }
@@ -47,6 +65,24 @@ struct Nbr {
     __device__ __forceinline__ int at(int di, int dj, int dk) const {
         if (inner) return idx + di + dj * nx + (DIM == 3 ? dk * sz : 0);
         return (km[dk + 3] * ny + jm[dj + 3]) * nx + im[di + 3];
+    }
+    // neighbour of a y-face quantity (periodic wrap in y also with walls)
+    __device__ __forceinline__ int atv(int di, int dj, int dk) const {
+        if (inner) return at(di, dj, dk);
+        return (km[dk + 3] * ny + wrapi(cj + dj, ny)) * nx + im[di + 3];
+    }
+    // neighbour for a load of velocity component comp
+    __device__ __forceinline__ int atc(int comp, int di, int dj, int dk) const {
+        return comp == 1 ? atv(di, dj, dk) : at(di, dj, dk);
+    }
+    __device__ __forceinline__ int axc(int comp, int d, int o) const {
+        return d == 0 ? atc(comp, o, 0, 0) : (d == 1 ? atc(comp, 0, o, 0) : atc(comp, 0, 0, o));
+    }
+    __device__ __forceinline__ int ax2c(int comp, int d1, int o1, int d2, int o2) const {
+        int di = (d1 == 0 ? o1 : 0) + (d2 == 0 ? o2 : 0);
+        int dj = (d1 == 1 ? o1 : 0) + (d2 == 1 ? o2 : 0);
+        int dk = (d1 == 2 ? o1 : 0) + (d2 == 2 ? o2 : 0);
+        return atc(comp, di, dj, dk);
     }
     // offset o along axis d
     __device__ __forceinline__ int ax(int d, int o) const {

@@ -18,6 +18,7 @@ constexpr int kThreads = 256;
 struct Dims {
     int nx, ny, nz;
     int ncell;
+    int wall_y;               // 1: free-slip walls at y = 0 and y = ny h (2D), else periodic
     double h;
     double ih, i2h, ih2;      // 1/h, 1/(2h), 1/h^2
     float ihf, i2hf, ih2f;
@@ -28,6 +29,7 @@ inline Dims make_dims(int nx, int ny, int nz, double h) {
     g.ny = ny;
     g.nz = nz;
     g.ncell = nx * ny * nz;
+    g.wall_y = 0;
     g.h = h;
     g.ih = 1.0 / h;
     g.i2h = 0.5 / h;
@@ -223,7 +225,7 @@ struct Prof {
 
 // ---- launch wrappers (defined in the .cu files) ----
 template <typename T, int DIM>
-void launch_init_phi(const Dims& g, const Phys& ph, double R, int mode, double amp, T* phi,
+void launch_init_phi(const Dims& g, const Phys& ph, double R, int mode, double amp, int shape, T* phi,
                      cudaStream_t s);
 template <typename T>
 void launch_convert_in(const double* src, T* dst, int n, cudaStream_t s);

@@ -36,6 +36,11 @@ __device__ __forceinline__ void face_w(const MGLevel<T>& L, const T* __restrict_
 #pragma unroll
         for (int q = 0; q < 2 * DIM; ++q)
             w[q] = T(beta_face32(pc, float(__ldg(phi + nb.m[q])), ph)) * ih2;
+        if (L.g.wall_y) {
+            const int j = (idx / L.g.nx) % L.g.ny;
+            if (wall_face(L.g, j, 2)) w[2] = T(0);
+            if (wall_face(L.g, j, 3)) w[3] = T(0);
+        }
     } else {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -221,8 +226,10 @@ k_coarsen_beta(MGLevel<T> F, MGLevel<T> C, const T* __restrict__ phi, Phys ph) {
                     T bf;
                     if (F.beta[0] == nullptr) {
                         const Nb6 nb = nb6<DIM>(F.g, fi, fj, fk, fidx);
-                        bf = T(beta_face32(float(__ldg(phi + fidx)), float(__ldg(phi + nb.m[2 * d])),
-                                           ph));
+                        bf = wall_face(F.g, fj, 2 * d)
+                                 ? T(0)
+                                 : T(beta_face32(float(__ldg(phi + fidx)),
+                                                 float(__ldg(phi + nb.m[2 * d])), ph));
                     } else {
                         bf = F.beta[d][fidx];
                     }
@@ -245,7 +252,9 @@ k_beta0(Dims g, Phys ph, const T* __restrict__ phi, double* __restrict__ b0,
         double* bb[3] = {b0, b1, b2};
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-            bb[d][idx] = 1.0 / (0.5 * (rc + rho_of_p(double(__ldg(phi + nb.m[2 * d])), pc)));
+            bb[d][idx] = wall_face(g, j, 2 * d)
+                             ? 0.0
+                             : 1.0 / (0.5 * (rc + rho_of_p(double(__ldg(phi + nb.m[2 * d])), pc)));
     });
 }
 
@@ -261,7 +270,7 @@ k_beta0_32(Dims g, Phys ph, const float* __restrict__ phi, float* __restrict__ b
         const float pc = __ldg(phi + idx);
         if (rho) rho[idx] = rho32(pc, ph);
         b0[idx] = beta_face32(pc, __ldg(phi + nb.m[0]), ph);
-        b1[idx] = beta_face32(pc, __ldg(phi + nb.m[2]), ph);
+        b1[idx] = wall_face(g, j, 2) ? 0.f : beta_face32(pc, __ldg(phi + nb.m[2]), ph);
         if (DIM == 3) b2[idx] = beta_face32(pc, __ldg(phi + nb.m[4]), ph);
     });
 }
@@ -633,7 +642,9 @@ __device__ __forceinline__ double apply_A64(const Dims& g, const Phys& ph,
         const float pc = float(__ldg(io.phi + idx));
 #pragma unroll
         for (int q = 0; q < 2 * DIM; ++q)
-            ax += double(beta_face32(pc, float(__ldg(io.phi + nb.m[q])), ph)) * (xc - x[nb.m[q]]);
+            if (!wall_face(g, j, q))
+                ax += double(beta_face32(pc, float(__ldg(io.phi + nb.m[q])), ph)) *
+                      (xc - x[nb.m[q]]);
     }
     return ax * ih2;
 }
@@ -682,7 +693,7 @@ k_ir_residual(Dims g, Phys ph, SolveIO<T, DIM> io, int first, RedBuf rb, CGScala
                 if (io.beta32[0] != nullptr)
                     beta = __ldg(io.beta32[q >> 1] + ((q & 1) ? m : idx));
                 else
-                    beta = beta_face32(pc, float(__ldg(io.phi + m)), ph);
+                    beta = wall_face(g, j, q) ? 0.f : beta_face32(pc, float(__ldg(io.phi + m)), ph);
                 df_face_term(beta, xch, xcl, xh[m], xl[m], S, c);
             }
             const f2 ax = f2_mul(two_sum(S, c), ih2);
@@ -815,7 +826,8 @@ k_in_dir(Dims g, Phys ph, SolveIO<T, DIM> io, int cur, int first_arg, RedBuf rb,
             for (int q = 0; q < 2 * DIM; ++q) {
                 const int m = nb.m[q];
                 const T pm = first ? io.z[m] : io.z[m] + beta * po[m];
-                ax += T(beta_face32(phc, float(__ldg(io.phi + m)), ph)) * (pc - pm);
+                if (!wall_face(g, j, q))
+                    ax += T(beta_face32(phc, float(__ldg(io.phi + m)), ph)) * (pc - pm);
             }
         }
         ax *= ih2;

@@ -39,12 +39,21 @@ __device__ __forceinline__ T mom_to_vel(T mom, T pa, T pb, const Phys& ph) {
 __device__ __forceinline__ double dpsi64(double p) { return p * (1.0 - p) * (1.0 - 2.0 * p); }
 
 // ---------------------------------------------------------------------------
-// initial profile phi0 = [1 + tanh((R(theta) - r) / (2 eps))] / 2
+// initial profile phi0 = [1 + tanh(s / (2 eps))] / 2, s the signed distance:
+// drop, s = R(theta) - r; wave (2D), s = y_i(x) - y with the interface height
+// y_i = R (1 - a cos(k (x - h/2))), k = 2 pi mode / (nx h), phi = 1 below it
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void k_init_phi(Dims g, Phys ph, double R, int mode, double amp, T* __restrict__ phi) {
+__global__ void k_init_phi(Dims g, Phys ph, double R, int mode, double amp, int shape,
+                           T* __restrict__ phi) {
     for_cells(g, [&](int ci, int cj, int ck, int idx) {
     Cell c{ci, cj, ck};
+    if (shape == 1) {
+        const double kx = 2.0 * 3.14159265358979323846 * mode / (g.nx * g.h);
+        const double yi = R * (1.0 - amp * cos(kx * (c.i * g.h)));
+        phi[idx] = T(0.5 * (1.0 + tanh((yi - (c.j + 0.5) * g.h) / (2.0 * ph.eps))));
+        return;
+    }
     double cx = 0.5 * g.nx * g.h, cy = 0.5 * g.ny * g.h, cz = 0.5 * g.nz * g.h;
     double x = (c.i + 0.5) * g.h - cx, y = (c.j + 0.5) * g.h - cy;
     double z = DIM == 3 ? (c.k + 0.5) * g.h - cz : 0.0;
@@ -70,10 +79,10 @@ __global__ void k_init_phi(Dims g, Phys ph, double R, int mode, double amp, T* _
 }
 
 template <typename T, int DIM>
-void launch_init_phi(const Dims& g, const Phys& ph, double R, int mode, double amp, T* phi,
-                     cudaStream_t s) {
+void launch_init_phi(const Dims& g, const Phys& ph, double R, int mode, double amp, int shape,
+                     T* phi, cudaStream_t s) {
     k_init_phi<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(g, ph, R, mode, amp,
-                                                                            phi);
+                                                                            shape, phi);
 }
 
 template <typename T>
@@ -231,7 +240,11 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
             T pp = ldg(phi, ip);
             T pf2 = T(0.5) * (pp + pc);
             T nf2 = T(0.5) * (ldg(nd, ip) + ldg(nd, idx));
-            T Fhi = ldg(ud, ip) * pf2 - gam * (eps * ((pp - pc) * inv_h) - pf2 * (T(1) - pf2) * nf2);
+            T Fhi = ldg(ud, nb.axc(d, d, 1)) * pf2 -
+                    gam * (eps * ((pp - pc) * inv_h) - pf2 * (T(1) - pf2) * nf2);
+            // no flux through a wall
+            if (wall_face(g, c.j, 2 * d)) Flo = T(0);
+            if (wall_face(g, c.j, 2 * d + 1)) Fhi = T(0);
             kphi = kphi - (Fhi - Flo) * inv_h;
         }
     } else {
@@ -243,7 +256,9 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
             int ip = nb.ax(d, 1);
             T pp = ldg(phi, ip);
             T Flo = ldg(ud, idx) * (T(0.5) * (pc + pm));
-            T Fhi = ldg(ud, ip) * (T(0.5) * (pp + pc));
+            T Fhi = ldg(ud, nb.axc(d, d, 1)) * (T(0.5) * (pp + pc));
+            if (wall_face(g, c.j, 2 * d)) Flo = T(0);
+            if (wall_face(g, c.j, 2 * d + 1)) Fhi = T(0);
             kphi = kphi - (Fhi - Flo) * inv_h;
             lap = lap + (pp - T(2) * pc + pm) * inv_h2;
             T gd = (pp - pm) * inv2h;
@@ -277,10 +292,10 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
                     vel = udc;
                 } else {
                     const T* __restrict__ ue = io.u_s[e];
-                    vel = T(0.25) * (ldg(ue, idx) + ldg(ue, nb.ax(e, 1)) + ldg(ue, im) +
-                                     ldg(ue, nb.ax2(d, -1, e, 1)));
+                    vel = T(0.25) * (ldg(ue, idx) + ldg(ue, nb.axc(e, e, 1)) + ldg(ue, im) +
+                                     ldg(ue, nb.ax2c(e, d, -1, e, 1)));
                 }
-                adv = adv + vel * ((ldg(ud, nb.ax(e, 1)) - ldg(ud, nb.ax(e, -1))) * inv2h);
+                adv = adv + vel * ((ldg(ud, nb.axc(d, e, 1)) - ldg(ud, nb.axc(d, e, -1))) * inv2h);
             }
         } else {
             // consistent transport: div(m u_d) in flux form, m the mass flux
@@ -329,7 +344,7 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
 #pragma unroll
         for (int e = 0; e < DIM; ++e) {
             if (e == d) {
-                T thi = T(2) * etac * ((ldg(ud, nb.ax(d, 1)) - udc) * inv_h);
+                T thi = T(2) * etac * ((ldg(ud, nb.axc(d, d, 1)) - udc) * inv_h);
                 T tlo = T(2) * etam * ((udc - ldg(ud, im)) * inv_h);
                 visc = visc + (thi - tlo) * inv_h;
             } else {
@@ -337,14 +352,15 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
                 // edge at (c - e_d/2 - e_e/2): cells c, c-e_d, c-e_e, c-e_d-e_e
                 T eta_lo = T(0.25) * (etac + etam + eta_of(ldg(phi, nb.ax(e, -1)), pcs) +
                                       eta_of(ldg(phi, nb.ax2(d, -1, e, -1)), pcs));
-                T tlo = eta_lo * ((udc - ldg(ud, nb.ax(e, -1))) * inv_h +
+                T tlo = eta_lo * ((udc - ldg(ud, nb.axc(d, e, -1))) * inv_h +
                                   (ldg(ue, idx) - ldg(ue, im)) * inv_h);
                 // edge at (c - e_d/2 + e_e/2): cells c+e_e, c+e_e-e_d, c, c-e_d
                 const int iep = nb.ax(e, 1), iepm = nb.ax2(d, -1, e, 1);
                 T eta_hi = T(0.25) * (eta_of(ldg(phi, iep), pcs) + eta_of(ldg(phi, iepm), pcs) +
                                       etac + etam);
-                T thi = eta_hi * ((ldg(ud, iep) - udc) * inv_h +
-                                  (ldg(ue, iep) - ldg(ue, iepm)) * inv_h);
+                T thi = eta_hi * ((ldg(ud, nb.axc(d, e, 1)) - udc) * inv_h +
+                                  (ldg(ue, nb.axc(e, e, 1)) - ldg(ue, nb.ax2c(e, d, -1, e, 1))) *
+                                      inv_h);
                 visc = visc + (thi - tlo) * inv_h;
             }
         }
@@ -368,6 +384,7 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
         } else {
             ku[d] = -adv + visc + F;   // d(rho_f u_d)/dt
         }
+        if (wall_face(g, c.j, 2 * d)) ku[d] = T(0);   // the wall's normal velocity stays 0
     }
     (void)h;
 
@@ -768,8 +785,9 @@ k_correct(Dims g, Phys ph, const T* __restrict__ phi, const double* __restrict__
                 // float32 path: same beta as the pressure operator; the pressure
                 // is a double-float (hi plane, lo plane), its difference formed
                 // from both parts, scaled and applied in float32
-                const float beta = f0 != nullptr ? __ldg(fv[d] + idx)
-                                                 : beta_face32(float(phi[idx]), float(phi[m]), ph);
+                const float beta = f0 != nullptr        ? __ldg(fv[d] + idx)
+                                   : wall_face(g, j, 2 * d) ? 0.f
+                                                            : beta_face32(float(phi[idx]), float(phi[m]), ph);
                 const float* ph_ = reinterpret_cast<const float*>(p);
                 const float* pl_ = ph_ + g.ncell;
                 const float gp =
@@ -826,7 +844,8 @@ k_diag(Dims g, Phys ph, const T* __restrict__ phi, const T* __restrict__ u0,
             double ud = double(uv[d][idx]);
             ke += 0.5 * rf * ud * ud;
             umax = fmax(umax, fabs(ud));
-            double df = (pc - pm) * inv_h;
+            // no gradient across a wall (the image cell mirrors phi)
+            double df = wall_face(g, cj, 2 * d) ? 0.0 : (pc - pm) * inv_h;
             grad2 += df * df;
             if (!isfinite(ud)) bad += 1.0;
         }
@@ -932,7 +951,7 @@ void launch_sub_mean(double* x, int n, const double* sum_ptr, double inv_n, cuda
 // explicit instantiations
 // ---------------------------------------------------------------------------
 #define PF_INST_TD(T, D)                                                                        \
-    template void launch_init_phi<T, D>(const Dims&, const Phys&, double, int, double, T*,      \
+    template void launch_init_phi<T, D>(const Dims&, const Phys&, double, int, double, int, T*, \
                                         cudaStream_t);                                          \
     template void launch_cell_pass<T, D>(const Dims&, const Phys&, const T*, T*, T*, T*, T*,    \
                                          cudaStream_t);                                         \

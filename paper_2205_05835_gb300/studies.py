@@ -28,6 +28,17 @@ reporting the spurious currents, the Laplace pressure jump against sigma / R
 and the mixed path's per-field distance from the float64 run of the same force:
 
     python -m paper_2205_05835_gb300.studies --compare --steps 2000
+
+A third driver runs the standing wave of Section 3.2 (2 pi x 2 pi box,
+periodic in x, free-slip walls in y, sigma = 2, rho = 1, nu = 0.064720863,
+initial amplitude A0 = 2 pi / 100, one wavelength) for every force on a mesh
+sequence at fixed eps = (2 pi) / 32 ("h", Figs. 6 and 7 a-c) or on the
+sharp-interface sequence dx = 32^(1/2) eps^(3/2) ("eps", Figs. 6 and 7 d),
+and reports the amplitude A(t) / lambda at x = dx/2, its l2 distance from the
+viscous initial-value solution of Prosperetti (1981) and the kinetic,
+surface and total energy histories (Fig. 8):
+
+    python -m paper_2205_05835_gb300.studies --wave h --ns 16,32,64,128
 """
 from __future__ import annotations
 
@@ -155,6 +166,119 @@ def force_precision_comparison(n=256, steps=2000, forces=("eb", "csf", "lcsf"),
     return out
 
 
+def prosperetti_amplitude(t, k, nu, sigma, rho1, rho2):
+    """Amplitude a(t) / a(0) of a small capillary wave of wavenumber k between
+    two unbounded fluids of equal kinematic viscosity nu, released from rest
+    (Prosperetti 1981, the exact solution the paper's Section 3.2 compares
+    with):
+
+      a / a0 = 4 (1 - 4 b) nu^2 k^4 / (8 (1 - 4 b) nu^2 k^4 + w0^2) erfc(sqrt(nu k^2 t))
+               + sum_i z_i w0^2 / (Z_i (z_i^2 - nu k^2)) exp((z_i^2 - nu k^2) t) erfc(z_i sqrt t)
+
+    with b = rho1 rho2 / (rho1 + rho2)^2, w0^2 = sigma k^3 / (rho1 + rho2),
+    z_i the four roots of
+      z^4 - 4 b (k^2 nu)^(1/2) z^3 + 2 (1 - 6 b) k^2 nu z^2
+          + 4 (1 - 3 b) (k^2 nu)^(3/2) z + (1 - 4 b) nu^2 k^4 + w0^2 = 0
+    and Z_i = prod_{j != i} (z_j - z_i). exp(z^2 t) erfc(z sqrt t) is
+    evaluated as the scaled complementary error function w(i z sqrt t)
+    (Faddeeva), which stays finite where the two factors would not.
+    """
+    import numpy as np
+    from scipy.special import erfc, wofz
+
+    b = rho1 * rho2 / (rho1 + rho2) ** 2
+    w02 = sigma * k ** 3 / (rho1 + rho2)
+    nk = k * k * nu
+    z = np.roots([1.0, -4.0 * b * math.sqrt(nk), 2.0 * (1.0 - 6.0 * b) * nk,
+                  4.0 * (1.0 - 3.0 * b) * nk ** 1.5, (1.0 - 4.0 * b) * nk * nk + w02])
+    t = np.asarray(t, dtype=np.float64)
+    a = (4.0 * (1.0 - 4.0 * b) * nk * nk / (8.0 * (1.0 - 4.0 * b) * nk * nk + w02)
+         * erfc(np.sqrt(nk * t))).astype(np.complex128)
+    for i in range(4):
+        Zi = np.prod([z[j] - z[i] for j in range(4) if j != i])
+        a = a + z[i] * w02 / (Zi * (z[i] ** 2 - nk)) * np.exp(-nk * t) * wofz(1j * z[i] * np.sqrt(t))
+    return a.real
+
+
+def wave_eps(panel, n):
+    """Interface thickness of the standing-wave study on an n x n mesh of the
+    2 pi box: eps = 2 pi / 32 ("h"), or dx = 32^(1/2) eps^(3/2) in units of the
+    box edge ("eps")."""
+    L = 2.0 * math.pi
+    if panel == "h":
+        return L / 32.0
+    return L * (1.0 / (n * math.sqrt(32.0))) ** (2.0 / 3.0)
+
+
+def standing_wave_study(panel="h", ns=(16, 32, 64, 128), forces=("eb", "csf", "lcsf"),
+                        model="cdi", t_end=10.0, sample_dt=0.03, precision="fp64",
+                        use_graph=1):
+    """Every force on every mesh as one batch; per instance the amplitude
+    history A(t) / lambda at x = dx/2 (A = y0 minus the column integral of phi),
+    its l2 distance from prosperetti_amplitude over the samples, and the
+    KE / SE / TE histories."""
+    import numpy as np
+
+    import paper_2205_05835_gb300 as pf
+    import pf_inputs as I
+
+    plist, keys = [], []
+    for f in forces:
+        for n in ns:
+            p = I.standing_wave(n=n, force=f, model=model, precision=precision,
+                                eps_frac=wave_eps(panel, n) / (2.0 * math.pi))
+            p["use_graph"] = use_graph
+            plist.append(p)
+            keys.append((f, n))
+    bat = pf.Batch(plist)
+    lam = 2.0 * math.pi
+    every = [max(1, int(round(sample_dt / p["dt"]))) for p in plist]
+    nsamp = int(math.ceil(t_end / sample_dt))
+    hist = [{"t": [], "A": [], "ke": [], "se": []} for _ in plist]
+
+    def sample():
+        for i, p in enumerate(plist):
+            h = p["L"] / p["n"][0]
+            col = float(np.sum(bat.field(i, "phi")[:, 0])) * h
+            d = bat.diagnostics(i)
+            hist[i]["t"].append(d["t"])
+            hist[i]["A"].append((p["R"] - col) / lam)
+            hist[i]["ke"].append(d["ke"])
+            hist[i]["se"].append(d["se"])
+
+    t0 = time.perf_counter()
+    sample()
+    for _ in range(nsamp):
+        bat.step_each(every)
+        sample()
+    wall = time.perf_counter() - t0
+    bat.close()
+    out = {"panel": panel, "model": model, "precision": precision, "t_end": t_end,
+           "wall_s": wall, "ns": list(ns), "eps": {n: wave_eps(panel, n) for n in ns},
+           "l2": {}, "first_zero": {}, "runs": {}}
+    A0 = 2.0 * math.pi / 100.0
+    for i, (f, n) in enumerate(keys):
+        t = np.array(hist[i]["t"])
+        A = np.array(hist[i]["A"])
+        ex = A0 / lam * prosperetti_amplitude(t, 1.0, plist[i]["mu_in"], plist[i]["sigma"],
+                                              1.0, 1.0)
+        l2 = float(np.sqrt(np.mean((A[1:] - ex[1:]) ** 2)))
+        zc = np.where((A[:-1] >= 0) & (A[1:] < 0))[0]
+        tz = float(t[zc[0]] - A[zc[0]] * (t[zc[0] + 1] - t[zc[0]]) / (A[zc[0] + 1] - A[zc[0]])) \
+            if len(zc) else float("nan")
+        out["l2"].setdefault(f, {})[n] = l2
+        out["first_zero"].setdefault(f, {})[n] = tz
+        ke, se = np.array(hist[i]["ke"]), np.array(hist[i]["se"])
+        out["runs"][f"{f}-{n}"] = {"dt": plist[i]["dt"], "t": t.tolist(), "A_over_lambda": A.tolist(),
+                                    "exact": ex.tolist(), "ke": ke.tolist(), "se": se.tolist(),
+                                    "te": (ke + se).tolist()}
+    t_ex = np.linspace(0.0, t_end, 200001)
+    a_ex = prosperetti_amplitude(t_ex, 1.0, 0.064720863, 2.0, 1.0, 1.0)
+    z = np.where((a_ex[:-1] >= 0) & (a_ex[1:] < 0))[0]
+    out["first_zero_exact"] = float(t_ex[z[0]]) if len(z) else float("nan")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--panel", choices=("h", "eps"), default="h")
@@ -168,7 +292,21 @@ def main():
                     help="forces x precisions on the density-ratio-1000 drop")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--wave", choices=("h", "eps"), default=None,
+                    help="standing wave (Section 3.2) on the given mesh sequence")
+    ap.add_argument("--t-end", type=float, default=10.0)
+    ap.add_argument("--wave-precision", default="fp64")
+    ap.add_argument("--full", action="store_true", help="include the histories in the output")
     args = ap.parse_args()
+    if args.wave:
+        res = standing_wave_study(panel=args.wave, ns=tuple(int(v) for v in args.ns.split(",")),
+                                  forces=tuple(args.forces.split(",")),
+                                  model=args.models.split(",")[0], t_end=args.t_end,
+                                  precision=args.wave_precision)
+        if not args.full:
+            res.pop("runs")
+        print(json.dumps(res))
+        return
     if args.compare:
         print(json.dumps(force_precision_comparison(n=args.n, steps=args.steps)))
         return

@@ -24,6 +24,7 @@ FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 SCHEMES = {"rk4": 0, "fe": 1}
 MOMENTUM = {"advective": 0, "consistent": 1}
+SHAPES = {"drop": 0, "wave": 1}
 
 BATCH_SEED = 20261203
 
@@ -34,6 +35,7 @@ def _base(**kw):
         model="cdi", force="eb", precision="fp64", scheme="rk4",
         sigma=1.0, eps=None, rho_in=1.0, rho_out=1.0, mu_in=0.1, mu_out=0.1,
         gamma_fixed=0.0, gamma_min=0.0, dt=None, delta_n=1e-12, momentum="advective",
+        wall_y=0, shape="drop",
         poisson_rtol=1e-12, poisson_maxit=200,
         R=0.25, pert_mode=0, pert_amp=0.0, steps=1,
     )
@@ -130,6 +132,27 @@ def batch_manifest(count=256, seed=BATCH_SEED, precision="mixed", poisson_rtol=1
                                   pert_amp=0.05 if osc else 0.0, steps=1000,
                                   precision=precision, poisson_rtol=poisson_rtol)))
     return out
+
+
+def standing_wave(n=64, force="eb", model="cdi", precision="fp64", eps_frac=1.0 / 32,
+                  steps=1000, **kw):
+    """Section 3.2 standing wave on an n x n grid: a 2 pi x 2 pi box, periodic in
+    x, free-slip walls at y = 0 and y = 2 pi; interface y = pi - A0 cos(x - dx/2)
+    with A0 = 2 pi / 100 (one wavelength across the box), sigma = 2,
+    rho = 1 and nu = 0.064720863 in both phases, dt = 0.003 unless the
+    stability bound of suggest_dt is smaller. eps = eps_frac * 2 pi: the
+    paper's eps = 1/32 is read in units of the box edge (it quotes
+    eps / dx = 2 on the 64 x 64 mesh)."""
+    L = 2.0 * math.pi
+    nu = 0.064720863
+    p = _base(dim=2, n=(n, n, 1), L=L, model=model, force=force, precision=precision,
+              sigma=2.0, rho_in=1.0, rho_out=1.0, mu_in=nu, mu_out=nu, eps=eps_frac * L,
+              R=math.pi, pert_mode=1, pert_amp=0.02, shape="wave", wall_y=1, steps=steps,
+              poisson_rtol=1e-12 if precision == "fp64" else 1e-10)
+    p.update(kw)
+    if p["dt"] is None:
+        p["dt"] = min(0.003, suggest_dt(p))
+    return finalize(p)
 
 
 def small_case(dim=2, n=32, **kw):

@@ -180,3 +180,28 @@ def test_momentum_transport_validation(pf):
     q = pf.make_params(I.small_case(dim=2, n=32, momentum="consistent"))
     with pytest.raises(pf.PFError):
         pf.B.pf_adjoint_workspace_size(q)
+
+
+def test_wall_and_shape_validation(pf):
+    """Free-slip walls in y: 2D with advective transport; the standing-wave
+    shape needs them; the adjoint covers the periodic box only."""
+    import pf_inputs as I
+
+    ok = pf.make_params(I.standing_wave(n=32))
+    assert ok.wall_y == 1 and ok.shape == 1
+    assert pf.pf_workspace_size(ok) > 0
+    bad = [I.standing_wave(n=32, momentum="consistent"),
+           I.small_case(dim=3, n=16, wall_y=1),
+           I.small_case(dim=2, n=32, shape="wave"),
+           I.small_case(dim=2, n=32, wall_y=2)]
+    for b in bad:
+        with pytest.raises(pf.PFError) as e:
+            pf.pf_workspace_size(pf.make_params(b))
+        assert e.value.status == pf.B.PF_ERR_INVALID
+    q = pf.make_params(I.small_case(dim=2, n=32))
+    q.shape = 2
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(q)
+    with pytest.raises(pf.PFError) as e:
+        pf.B.pf_adjoint_workspace_size(ok)
+    assert e.value.status == pf.B.PF_ERR_INVALID

@@ -1,0 +1,153 @@
+"""Free-slip walls in y on the GPU (the standing wave of Section 3.2).
+
+Parity of the float64 path with the walled oracle (every field to 1e-10 after
+a few steps, for each model and force, RK4 and forward Euler, on grids whose
+multigrid hierarchy ends on odd-sized levels); the wall conditions on the
+GPU's own output (zero normal velocity on the wall faces, exact conservation
+of phi, a divergence-free velocity); mixed precision against float64; graph
+replay against host-driven stepping; and the standing wave's amplitude
+against the exact viscous solution on a resolved mesh.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import pf_inputs as I
+from oracle import pf_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2205_05835_gb300 as pf
+
+    return pf
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def walled(n, **kw):
+    base = dict(dim=2, n=(n[0], n[1], 1), L=1.0, wall_y=1, shape="wave",
+                R=0.5 * n[1] / n[0], pert_mode=1, pert_amp=0.1, rho_in=3.0, rho_out=1.0,
+                mu_in=0.02, mu_out=0.01, poisson_rtol=1e-13, poisson_maxit=400)
+    base.update(kw)
+    return I.finalize(I._base(**base))
+
+
+def start(p, seed):
+    g = O.Grid(2, p["n"], p["L"])
+    phi = O.initial_phi(O.params_from(p)) + 0.02 * (I.noise(g.shape, seed) - 0.5)
+    u = 0.1 * (I.noise(g.shape, seed + 1) - 0.5)
+    v = 0.1 * (I.noise(g.shape, seed + 2) - 0.5)
+    v[0, :] = 0.0
+    return phi, u, v
+
+
+@pytest.mark.parametrize("n,model,force,scheme", [
+    ((32, 24), "cdi", "eb", "rk4"), ((32, 24), "cdi", "csf", "rk4"),
+    ((40, 36), "cdi", "lcsf", "rk4"), ((32, 24), "sb", "eb", "fe"),
+    ((24, 40), "isodi", "lcsf", "rk4")])
+def test_walled_parity_fp64(pf, n, model, force, scheme):
+    p = walled(n, model=model, force=force, scheme=scheme, gamma_fixed=0.2)
+    po = O.params_from(p)
+    phi, u, v = start(p, 21)
+    sim = pf.Simulation(p, phi0=phi)
+    sim.set_field("u", u)
+    sim.set_field("v", v)
+    st = O.State(phi.copy(), [u.copy(), v.copy()], np.zeros(phi.shape))
+    for _ in range(4):
+        st = O.step(st, po)
+    sim.step(4)
+    assert rel(sim.field("phi"), st.phi) < TOL64
+    assert rel(sim.field("u"), st.u[0]) < TOL64
+    assert rel(sim.field("v"), st.u[1]) < TOL64
+    assert rel(sim.field("p"), st.p - st.p.mean()) < TOL64
+    d, od = sim.diagnostics(), O.diagnostics(st, po)
+    for k in ("mass", "ke", "se", "umax"):
+        assert abs(d[k] - od[k]) <= 1e-10 * abs(od[k]) + 1e-300, k
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_wall_conditions_on_gpu(pf, precision):
+    p = I.standing_wave(n=64, precision=precision)
+    sim = pf.Simulation(p)
+    m0 = sim.diagnostics()["mass"]
+    sim.step(50)
+    v = sim.field("v")
+    assert np.all(v[0] == 0.0)
+    d = sim.diagnostics()
+    assert abs(d["mass"] / m0 - 1.0) < (1e-13 if precision == "fp64" else 1e-6)
+    g = O.Grid(2, p["n"], p["L"])
+    div = O.divergence([sim.field("u"), v], g)
+    umax = max(float(np.abs(sim.field("u")).max()), float(np.abs(v).max()))
+    assert np.abs(div).max() < (1e-9 if precision == "fp64" else 1e-4) * umax / g.h
+    sim.close()
+
+
+def test_walled_mixed_against_fp64(pf):
+    """Mixed precision after 100 steps of the 64^2 wave: stated bounds
+    phi < 1e-5, u, v < 1e-3, p < 1e-4 (max-norm relative)."""
+    a = pf.Simulation(I.standing_wave(n=64, precision="fp64"))
+    b = pf.Simulation(I.standing_wave(n=64, precision="mixed"))
+    a.step(100)
+    b.step(100)
+    errs = {c: rel(b.field(c), a.field(c)) for c in ("phi", "u", "v", "p")}
+    assert errs["phi"] < 1e-5, errs
+    assert errs["u"] < 1e-3 and errs["v"] < 1e-3, errs
+    assert errs["p"] < 1e-4, errs
+    a.close()
+    b.close()
+
+
+def test_walled_graph_mode_matches(pf):
+    p = I.standing_wave(n=48, precision="mixed")
+    a = pf.Simulation(p)
+    b = pf.Simulation(dict(p, use_graph=1))
+    a.step(5)
+    b.step(5)
+    for c in ("phi", "u", "v", "p"):
+        np.testing.assert_array_equal(a.field(c), b.field(c))
+    a.close()
+    b.close()
+
+
+def test_standing_wave_follows_exact_solution(pf):
+    """EB on the 128^2 mesh (eps / dx = 4): the amplitude at x = dx/2 over the
+    first 4 time units stays within 5 % of A0 of the viscous initial-value
+    solution, and its first zero lies within 5 % of the exact one."""
+    from paper_2205_05835_gb300.studies import prosperetti_amplitude
+
+    p = I.standing_wave(n=128, use_graph=1)
+    sim = pf.Simulation(p)
+    h = p["L"] / p["n"][0]
+    A0 = 2 * math.pi / 100
+    ts, As = [0.0], [A0]
+    every = int(round(0.03 / p["dt"]))
+    while ts[-1] < 4.0:
+        sim.step(every)
+        ts.append(sim.diagnostics()["t"])
+        As.append(p["R"] - float(np.sum(sim.field("phi")[:, 0])) * h)
+    ts, As = np.array(ts), np.array(As)
+    ex = A0 * prosperetti_amplitude(ts, 1.0, p["mu_in"], p["sigma"], 1.0, 1.0)
+    assert np.max(np.abs(As - ex)) < 0.05 * A0
+    i = np.where((As[:-1] >= 0) & (As[1:] < 0))[0][0]
+    tz = ts[i] - As[i] * (ts[i + 1] - ts[i]) / (As[i + 1] - As[i])
+    te = np.linspace(0, 4, 40001)
+    ae = prosperetti_amplitude(te, 1.0, p["mu_in"], p["sigma"], 1.0, 1.0)
+    tz_ex = te[np.where((ae[:-1] >= 0) & (ae[1:] < 0))[0][0]]
+    assert abs(tz / tz_ex - 1.0) < 0.05, (tz, tz_ex)
+    sim.close()

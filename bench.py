@@ -10,7 +10,9 @@ one replayed CUDA graph whose solver loops are device-driven. The state
 
 The JSON line also carries: the roofline of the dominant kernel class (timed
 with CUDA events inside the library's tracing hooks, in a host-driven pass of
-the same steps when the headline runs as graph replays), an end-to-end
+the same steps when the headline runs as graph replays), a whole-step figure
+(compulsory bytes of every finest-grid kernel class over the headline time,
+a lower bound that leaves out the coarse multigrid levels), an end-to-end
 number through the C ABI with the state copied from and to pinned host memory
 every step, the FP64 oracle timed on the host cores on a bounded sample, the
 SM clocks sampled during the timed region and the number of kernel launches.
@@ -220,8 +222,40 @@ def algo_bytes_per_cell(cls, dim, w):
         "divergence": d * w + 8,
         "mg_restrict": (2 + d) * w + w / (2 ** d),
         "mg_prolong": 2 * w + w / (2 ** d),
+        # float32 face coefficients (and cell densities) from phi
+        "beta0_f64": w + d * w + w,
+        # x += e with x a double-float (float64 path: float64) pressure
+        "ir_addcorr": 2 * (8 if w == 4 else w) + w,
+        "gamma": d * w,
     }
     return table.get(cls)
+
+
+# kernel classes that work on the finest grid (one launch covers every cell);
+# the coarse multigrid classes run on levels of 1/2^d, 1/4^d, ... the cells
+FINEST_CLASSES = ("mg_gs_level0", "cg_dir_spmv", "cg_update", "ir_residual_f64", "stage",
+                  "cell_pass", "correct", "divergence", "beta0_f64", "ir_addcorr", "gamma")
+
+
+def step_roofline(prof, ncell, dim, w, ms_total, ms_host, peak):
+    """Compulsory bytes of the finest-grid kernel classes over the whole timed
+    region (algorithmic bytes per cell x cells x launches), divided by the
+    headline time: a lower bound on the step's bandwidth use (the coarse
+    multigrid levels are left out), with the share of the host-driven step
+    time those classes take."""
+    tot_b, tot_ms = 0.0, 0.0
+    for cls in FINEST_CLASSES:
+        if cls in prof and prof[cls][0] > 0:
+            bpc = algo_bytes_per_cell(cls, dim, w)
+            tot_b += bpc * ncell * prof[cls][0]
+            tot_ms += prof[cls][1]
+    if tot_b == 0.0 or ms_total <= 0:
+        return None
+    achieved = tot_b / (ms_total / 1e3) / 1e9
+    return {"bound": "hbm", "bytes": tot_b, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "classes": [c for c in FINEST_CLASSES if c in prof],
+            "their_time_share": tot_ms / ms_host if ms_host > 0 else None,
+            "their_bandwidth_gbs": tot_b / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else None}
 
 
 def cpu_sample_rate(p, steps=2, n=16):
@@ -428,6 +462,7 @@ def run_ours(args, rank, world, local_rank):
                 "share_of_step": dom_ms / ms_h if ms_h > 0 else None,
                 "timed_in": ("host-driven pass of the same steps (CUDA events around "
                              "each launch)" if args.graph else "the timed steps")}
+    step_roof = step_roofline(prof, ncell, p["dim"], w, ms, ms_h, peak)
 
     # end to end through the C ABI: state from / to pinned host memory every step
     e2e = None
@@ -477,7 +512,8 @@ def run_ours(args, rank, world, local_rank):
                        "execution": ("one replayed CUDA graph per step (device-driven "
                                      "solver loops)" if args.graph else "host-driven"),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "roofline": roof, "step_roofline": step_roof, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk,
             "gpu_launches": launches,
             "gpu_launches_counted_in": ("host-driven pass of the same steps (a replay "
                                         "adds early-exit launches of the unrolled CG "

@@ -116,7 +116,11 @@ typedef struct {
                              PF_SHAPE_WAVE (needs wall_y = 1): phi = 1 below the interface
                              y = R (1 - pert_amp cos(k (x - dx/2))), k = 2 pi pert_mode / (n[0] dx)
                              (R: mean height, pert_amp: amplitude over R) */
-    int reserved[4];      /* must be zero */
+    int mg_coarse_cells;  /* multigrid levels of at most this many cells are solved together by
+                             one single-CTA V-cycle kernel (0: 4096; else 16 .. 2^20). A
+                             tuning knob: it changes the preconditioner, not the converged
+                             solution (see the package's autotune module) */
+    int reserved[3];      /* must be zero */
 } pf_params;
 
 typedef struct {

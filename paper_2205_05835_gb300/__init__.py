@@ -51,7 +51,8 @@ def make_params(p: dict) -> B.pf_params:
     for k in ("sigma", "eps", "rho_in", "rho_out", "mu_in", "mu_out", "gamma_fixed", "gamma_min",
               "dt", "delta_n", "poisson_rtol", "R", "pert_amp", "bound_tol", "inner_tol"):
         setattr(q, k, float(p.get(k, 0.0) or 0.0))
-    for k in ("poisson_maxit", "pert_mode", "mg_pre", "mg_post", "use_graph", "wall_y"):
+    for k in ("poisson_maxit", "pert_mode", "mg_pre", "mg_post", "use_graph", "wall_y",
+              "mg_coarse_cells"):
         setattr(q, k, int(p.get(k, 0) or 0))
     return q
 

@@ -1,0 +1,81 @@
+"""Autotuner of the multigrid launch shape of a grid.
+
+The tunables change the preconditioner of the pressure solve, never the
+converged answer (every candidate solves to the same poisson_rtol):
+
+  mg_coarse_cells -- levels of at most this many cells are handled together
+                     by one single-CTA V-cycle launch (fewer, longer launches
+                     against more, shorter ones);
+  mg_pre, mg_post -- red-black sweeps before and after the coarse correction
+                     (cheaper V-cycles against fewer CG iterations).
+
+Each candidate gets a fresh context on the same parameters, runs `warm`
+steps, then `steps` timed steps (pf_step synchronises, so the host clock
+brackets device work); the fastest candidate wins. Results are cached per
+signature in memory and, given a path, in a JSON file, so a batch of many
+instances tunes each grid size once.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+CANDIDATES = (
+    {"mg_coarse_cells": 1024, "mg_pre": 1, "mg_post": 1},
+    {"mg_coarse_cells": 4096, "mg_pre": 1, "mg_post": 1},
+    {"mg_coarse_cells": 16384, "mg_pre": 1, "mg_post": 1},
+    {"mg_coarse_cells": 4096, "mg_pre": 2, "mg_post": 2},
+)
+
+_cache: dict = {}
+
+
+def signature(p: dict) -> str:
+    """What the best launch shape depends on: the grid, precision, model,
+    force, density ratio, walls and execution mode."""
+    n = tuple(int(v) for v in p["n"])
+    ratio = round(float(p["rho_in"]) / float(p["rho_out"]), 6)
+    return json.dumps([int(p["dim"]), n, str(p.get("precision")), str(p.get("model")),
+                       str(p.get("force")), ratio, int(p.get("wall_y", 0) or 0),
+                       int(p.get("use_graph", 0) or 0)])
+
+
+def _time_candidate(pf, p: dict, cand: dict, steps: int, warm: int) -> float:
+    sim = pf.Simulation(dict(p, **cand))
+    try:
+        sim.step(warm)
+        t0 = time.perf_counter()
+        sim.step(steps)
+        return (time.perf_counter() - t0) / steps
+    finally:
+        sim.close()
+
+
+def tune(p: dict, candidates=CANDIDATES, steps: int = 2, warm: int = 1,
+         cache_path: str | None = None) -> dict:
+    """Best candidate for the parameters p: {"choice": {...}, "ms_per_step":
+    {candidate: ms}, "cached": bool}."""
+    import paper_2205_05835_gb300 as pf
+
+    key = signature(p)
+    if key not in _cache and cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            _cache.update(json.load(f))
+    if key in _cache:
+        return dict(_cache[key], cached=True)
+    times = {}
+    for c in candidates:
+        times[json.dumps(c, sort_keys=True)] = 1e3 * _time_candidate(pf, p, c, steps, warm)
+    best = min(times, key=times.get)
+    res = {"choice": json.loads(best), "ms_per_step": times}
+    _cache[key] = res
+    if cache_path:
+        with open(cache_path, "w") as f:
+            json.dump(_cache, f)
+    return dict(res, cached=False)
+
+
+def apply(p: dict, res: dict) -> dict:
+    """p with the tuned launch shape."""
+    return dict(p, **res["choice"])

@@ -51,7 +51,8 @@ class pf_params(ctypes.Structure):
         ("momentum", ctypes.c_int),
         ("wall_y", ctypes.c_int),
         ("shape", ctypes.c_int),
-        ("reserved", ctypes.c_int * 4),
+        ("mg_coarse_cells", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 

@@ -196,7 +196,11 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "the standing-wave shape needs walls in y";
         return PF_ERR_INVALID;
     }
-    for (int i = 0; i < 4; ++i)
+    if (p->mg_coarse_cells != 0 && (p->mg_coarse_cells < 16 || p->mg_coarse_cells > (1 << 20))) {
+        why = "mg_coarse_cells must be 0 or in 16 .. 2^20";
+        return PF_ERR_INVALID;
+    }
+    for (int i = 0; i < 3; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
     return PF_OK;
 }
@@ -297,8 +301,9 @@ struct ImplT final : Impl {
         }
         for (int l = 0; l < kMaxLevels; ++l) H.lev[l].x2 = nullptr;
         H.first_coarse = H.nlev - 1;
+        const int coarse_cells = prm.mg_coarse_cells > 0 ? prm.mg_coarse_cells : 4096;
         for (int l = 0; l < H.nlev; ++l)
-            if (H.lev[l].g.ncell <= 4096) { H.first_coarse = l; break; }
+            if (H.lev[l].g.ncell <= coarse_cells) { H.first_coarse = l; break; }
         H.pre = prm.mg_pre > 0 ? prm.mg_pre : 1;
         H.post = prm.mg_post > 0 ? prm.mg_post : 1;
         const Dims& cg = H.lev[H.nlev - 1].g;

@@ -295,8 +295,9 @@ constexpr size_t kCoarseSmemMax = 200 * 1024;   // staged coarse hierarchy, byte
 // One colour of a red-black sweep over a (small) level by threads t0, t0 + nt,
 // ...: item q = (row, m) with cell i = 2 m + parity(row) of the colour; all:
 // the other colour's cell of the pair is zeroed. Rows and positions come from
-// float reciprocals (exact: q < 2^12 on the levels this runs on, so q + 1/2
-// stays far from a multiple of the divisor after rounding).
+// float reciprocals: (q + 1/2) / n lies at least 1/(2n) from an integer and
+// the two roundings move it by at most (q + 1/2) 2^-23 / n, so the quotient
+// truncates exactly for q < 2^22 (levels up to 2^20 cells run here).
 template <typename T, int DIM>
 __device__ __forceinline__ void cta_cells(const Dims& g, int color, bool all, const MGLevel<T>& L,
                                           const T* phi, const Phys& ph, bool zero_start,
@@ -322,7 +323,7 @@ __device__ __forceinline__ void cta_cells(const Dims& g, int color, bool all, co
 }
 
 // Cell coordinates of a linear index on a small level by float reciprocals
-// (exact for idx < 2^12: idx + 1/2 stays far from a multiple of nx or ny).
+// (exact for idx < 2^22, by the argument given for the sweep items above).
 __device__ __forceinline__ Cell decode_small(int idx, const Dims& g, float inv_nx, float inv_ny) {
     Cell c;
     const int r = int((float(idx) + 0.5f) * inv_nx);

@@ -65,7 +65,7 @@ def test_workspace_size_and_validation(pf):
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
     bad = pf.make_params(I.static_drop_64())
-    bad.reserved[3] = 1
+    bad.reserved[2] = 1
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
 
@@ -205,3 +205,25 @@ def test_wall_and_shape_validation(pf):
     with pytest.raises(pf.PFError) as e:
         pf.B.pf_adjoint_workspace_size(ok)
     assert e.value.status == pf.B.PF_ERR_INVALID
+
+
+def test_mg_coarse_cells_validation_and_autotune_keys(pf):
+    """The coarse-solve threshold is 0 (default) or 16 .. 2^20; the autotuner's
+    cache key separates what the best launch shape depends on."""
+    import pf_inputs as I
+    from paper_2205_05835_gb300 import autotune
+
+    for v in (0, 16, 4096, 1 << 20):
+        assert pf.pf_workspace_size(pf.make_params(I.small_case(dim=2, n=32,
+                                                                mg_coarse_cells=v))) > 0
+    for v in (8, (1 << 20) + 1, -1):
+        with pytest.raises(pf.PFError) as e:
+            pf.pf_workspace_size(pf.make_params(I.small_case(dim=2, n=32, mg_coarse_cells=v)))
+        assert e.value.status == pf.B.PF_ERR_INVALID
+    a = I.small_case(dim=2, n=64)
+    assert autotune.signature(a) == autotune.signature(dict(a, sigma=3.0, R=0.2))
+    for other in (dict(n=(80, 80, 1)), dict(precision="mixed"), dict(rho_out=0.01),
+                  dict(use_graph=1), dict(force="csf")):
+        assert autotune.signature(dict(a, **other)) != autotune.signature(a)
+    tuned = autotune.apply(a, {"choice": autotune.CANDIDATES[2]})
+    assert tuned["mg_coarse_cells"] == 16384 and tuned["sigma"] == a["sigma"]

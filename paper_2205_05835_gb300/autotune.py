@@ -21,12 +21,9 @@ import json
 import os
 import time
 
-CANDIDATES = (
-    {"mg_coarse_cells": 1024, "mg_pre": 1, "mg_post": 1},
-    {"mg_coarse_cells": 4096, "mg_pre": 1, "mg_post": 1},
-    {"mg_coarse_cells": 16384, "mg_pre": 1, "mg_post": 1},
-    {"mg_coarse_cells": 4096, "mg_pre": 2, "mg_post": 2},
-)
+CANDIDATES = tuple(
+    [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (1, 2) for c in (1024, 4096, 16384)]
+    + [{"mg_coarse_cells": 4096, "mg_pre": 3, "mg_post": 3}])
 
 _cache: dict = {}
 

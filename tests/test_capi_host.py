@@ -225,5 +225,6 @@ def test_mg_coarse_cells_validation_and_autotune_keys(pf):
     for other in (dict(n=(80, 80, 1)), dict(precision="mixed"), dict(rho_out=0.01),
                   dict(use_graph=1), dict(force="csf")):
         assert autotune.signature(dict(a, **other)) != autotune.signature(a)
+    assert {"mg_coarse_cells": 16384, "mg_pre": 1, "mg_post": 1} in autotune.CANDIDATES
     tuned = autotune.apply(a, {"choice": autotune.CANDIDATES[2]})
     assert tuned["mg_coarse_cells"] == 16384 and tuned["sigma"] == a["sigma"]

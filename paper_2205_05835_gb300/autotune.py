@@ -23,7 +23,7 @@ import time
 
 CANDIDATES = tuple(
     [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (1, 2) for c in (1024, 4096, 16384)]
-    + [{"mg_coarse_cells": 4096, "mg_pre": 3, "mg_post": 3}])
+    + [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (3, 4) for c in (4096, 16384)])
 
 _cache: dict = {}
 

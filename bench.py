@@ -16,6 +16,9 @@ a lower bound that leaves out the coarse multigrid levels), an end-to-end
 number through the C ABI with the state copied from and to pinned host memory
 every step, the FP64 oracle timed on the host cores on a bounded sample, the
 SM clocks sampled during the timed region and the number of kernel launches.
+Before the timed region the multigrid launch shape (coarse-solve threshold,
+smoothing sweeps) is autotuned on the workload's grid, per grid size for the
+batch (`--autotune 0` keeps the defaults); the choice is in `config`.
 
 `--impl reference` times the FP64 oracle (the only reference there is: the
 paper has no code) on the host on a bounded sample of the same workload.

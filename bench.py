@@ -32,6 +32,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -134,7 +135,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples go to $PF_CLOCK_DIR (default: the temporary directory)
+        d = os.environ.get("PF_CLOCK_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_rank{index}.csv")
 
     def start(self):
         try:

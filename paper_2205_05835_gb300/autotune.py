@@ -7,7 +7,11 @@ converged answer (every candidate solves to the same poisson_rtol):
                      by one single-CTA V-cycle launch (fewer, longer launches
                      against more, shorter ones);
   mg_pre, mg_post -- red-black sweeps before and after the coarse correction
-                     (cheaper V-cycles against fewer CG iterations).
+                     (cheaper V-cycles against fewer CG iterations);
+  inner_tol       -- mixed precision only, tuned second with the best shape
+                     fixed: the residual reduction of each float32 inner
+                     solve between float64 refinements (fewer refinements
+                     against fewer inner iterations).
 
 Each candidate gets a fresh context on the same parameters, runs `warm`
 steps, then `steps` timed steps (pf_step synchronises, so the host clock
@@ -24,6 +28,8 @@ import time
 CANDIDATES = tuple(
     [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (1, 2) for c in (1024, 4096, 16384)]
     + [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (3, 4) for c in (4096, 16384)])
+
+INNER_TOLS = (1e-6, 1e-5, 1e-4, 1e-3)   # the first is the library's default
 
 _cache: dict = {}
 
@@ -65,7 +71,16 @@ def tune(p: dict, candidates=CANDIDATES, steps: int = 2, warm: int = 1,
     for c in candidates:
         times[json.dumps(c, sort_keys=True)] = 1e3 * _time_candidate(pf, p, c, steps, warm)
     best = min(times, key=times.get)
-    res = {"choice": json.loads(best), "ms_per_step": times}
+    choice = json.loads(best)
+    if p.get("precision") == "mixed" and not p.get("inner_tol"):
+        base_ms = times[best]
+        for tol in INNER_TOLS[1:]:
+            c = dict(choice, inner_tol=tol)
+            ms = 1e3 * _time_candidate(pf, p, c, steps, warm)
+            times[json.dumps(c, sort_keys=True)] = ms
+            if ms < base_ms:
+                base_ms, choice = ms, c
+    res = {"choice": choice, "ms_per_step": times}
     _cache[key] = res
     if cache_path:
         with open(cache_path, "w") as f:

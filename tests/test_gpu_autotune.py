@@ -49,8 +49,10 @@ def test_tune_picks_a_candidate_and_caches(pf):
 
     p = I.small_case(dim=2, n=128, precision="mixed", poisson_rtol=1e-10, use_graph=1)
     r = autotune.tune(p, steps=2, warm=1)
-    assert r["choice"] in list(autotune.CANDIDATES) and not r["cached"]
-    assert len(r["ms_per_step"]) == len(autotune.CANDIDATES)
+    shape = {k: v for k, v in r["choice"].items() if k != "inner_tol"}
+    assert shape in list(autotune.CANDIDATES) and not r["cached"]
+    assert r["choice"].get("inner_tol", 1e-6) in autotune.INNER_TOLS
+    assert len(r["ms_per_step"]) == len(autotune.CANDIDATES) + len(autotune.INNER_TOLS) - 1
     assert all(v > 0 for v in r["ms_per_step"].values())
     assert autotune.tune(p)["cached"]
     sim = pf.Simulation(autotune.apply(p, r))

@@ -8,10 +8,12 @@ converged answer (every candidate solves to the same poisson_rtol):
                      against more, shorter ones);
   mg_pre, mg_post -- red-black sweeps before and after the coarse correction
                      (cheaper V-cycles against fewer CG iterations);
-  inner_tol       -- mixed precision only, tuned second with the best shape
-                     fixed: the residual reduction of each float32 inner
-                     solve between float64 refinements (fewer refinements
-                     against fewer inner iterations).
+  inner_tol       -- optional (tune_inner), mixed precision only, tuned
+                     second with the best shape fixed: the residual reduction
+                     of each float32 inner solve between float64 refinements
+                     (fewer refinements against fewer inner iterations). On
+                     the uneven 2D batch it gave no gain beyond run-to-run
+                     spread, so it is off by default.
 
 Each candidate gets a fresh context on the same parameters, runs `warm`
 steps, then `steps` timed steps (pf_step synchronises, so the host clock
@@ -56,7 +58,7 @@ def _time_candidate(pf, p: dict, cand: dict, steps: int, warm: int) -> float:
 
 
 def tune(p: dict, candidates=CANDIDATES, steps: int = 2, warm: int = 1,
-         cache_path: str | None = None) -> dict:
+         cache_path: str | None = None, tune_inner: bool = False) -> dict:
     """Best candidate for the parameters p: {"choice": {...}, "ms_per_step":
     {candidate: ms}, "cached": bool}."""
     import paper_2205_05835_gb300 as pf
@@ -72,7 +74,7 @@ def tune(p: dict, candidates=CANDIDATES, steps: int = 2, warm: int = 1,
         times[json.dumps(c, sort_keys=True)] = 1e3 * _time_candidate(pf, p, c, steps, warm)
     best = min(times, key=times.get)
     choice = json.loads(best)
-    if p.get("precision") == "mixed" and not p.get("inner_tol"):
+    if tune_inner and p.get("precision") == "mixed" and not p.get("inner_tol"):
         base_ms = times[best]
         for tol in INNER_TOLS[1:]:
             c = dict(choice, inner_tol=tol)

@@ -48,7 +48,7 @@ def test_tune_picks_a_candidate_and_caches(pf):
     from paper_2205_05835_gb300 import autotune
 
     p = I.small_case(dim=2, n=128, precision="mixed", poisson_rtol=1e-10, use_graph=1)
-    r = autotune.tune(p, steps=2, warm=1)
+    r = autotune.tune(p, steps=2, warm=1, tune_inner=True)
     shape = {k: v for k, v in r["choice"].items() if k != "inner_tol"}
     assert shape in list(autotune.CANDIDATES) and not r["cached"]
     assert r["choice"].get("inner_tol", 1e-6) in autotune.INNER_TOLS

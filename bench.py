@@ -290,6 +290,29 @@ def cpu_sample_rate(p, steps=2, n=16):
     return cells * steps / dt / 1e6, cores, desc
 
 
+def cpu_batch_rate(plist, steps=1, max_n=96):
+    """The oracle on the batch's small instances (n <= max_n, at their own
+    sizes and parameters), one instance per task on a spawned pool over the
+    host cores: cells x steps / wall time of the pool (started and warmed
+    before the clock starts). Returns (Mcell-steps/s, cores, description)."""
+    import multiprocessing as mp
+
+    from oracle import pf_oracle as O
+
+    sample = [p for p in plist if p["n"][0] <= max_n]
+    cores = max(1, min(len(sample), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(O.timed_run, [(None, 0)] * cores)
+        t0 = time.perf_counter()
+        res = pool.map(O.timed_run, [(p, steps) for p in sample], chunksize=1)
+        wall = time.perf_counter() - t0
+    cells = sum(r[0] for r in res)
+    desc = (f"{steps} step(s) of each of the {len(sample)} instances with N <= {max_n} "
+            f"(float64 numpy oracle, sparse direct pressure solves), one instance per task "
+            f"on {cores} spawned processes")
+    return cells / wall / 1e6, cores, desc
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
     if rank != 0:
@@ -373,6 +396,10 @@ def run_batch(args, rank, world, local_rank):
     if dist is not None:
         wall = job_time(wall, dist, "cuda")
         dist.destroy_process_group()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sdesc = cpu_batch_rate(plist)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": total_cells * args.steps / wall / 1e6, "unit": UNIT,
@@ -390,7 +417,7 @@ def run_batch(args, rank, world, local_rank):
                        "timing": "host wall clock between device synchronisations, max over ranks",
                        "autotune": ({"choices": {str(k): v for k, v in tuned.items()},
                                      "tuning_s": t_tune} if tuned is not None else None)},
-            "clocks": clk}), flush=True)
+            "cpu_baseline": cpu, "clocks": clk}), flush=True)
 
 
 def run_ours(args, rank, world, local_rank):

@@ -653,6 +653,23 @@ def step(st, p):
             return State(phi_new, u_new, pr, st.step + 1, st.t + dt)
 
 
+def timed_run(job):
+    """(params, steps) -> (cells x steps, seconds): steps of the oracle from the
+    initial state, timed (a task of the host baseline's process pool; params
+    None is a no-op that warms a worker)."""
+    import time
+
+    p, steps = job
+    if p is None:
+        return 0, 0.0
+    p = params_from(dict(p, precision="fp64"))
+    st = initial_state(p)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = step(st, p)
+    return int(np.prod(Grid(p["dim"], p["n"], p["L"]).shape)) * steps, time.perf_counter() - t0
+
+
 def run(p, steps=None, phi0=None, record=False):
     p = params_from(p)
     st = initial_state(p, phi0)

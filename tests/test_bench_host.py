@@ -1,0 +1,39 @@
+"""Host-side pieces of bench.py: the whole-step roofline arithmetic and the
+multi-core oracle baseline of the batch workload (CPU only)."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_step_roofline_sums_finest_classes(bench):
+    # two classes on a 1000-cell grid: 16 B/cell x 10 launches and 28 B/cell x 5
+    prof = {"mg_gs_level0": (10, 2.0), "cg_dir_spmv": (5, 1.0), "mg_restrict": (50, 3.0)}
+    r = bench.step_roofline(prof, 1000, 3, 4, ms_total=4.0, ms_host=8.0, peak=100.0)
+    want_bytes = 16 * 1000 * 10 + 28 * 1000 * 5
+    assert r["bytes"] == want_bytes
+    assert r["achieved"] == pytest.approx(want_bytes / 4e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 100.0)
+    assert r["their_time_share"] == pytest.approx(3.0 / 8.0)   # the coarse class is left out
+    assert "mg_restrict" not in r["classes"]
+    assert bench.step_roofline({}, 1000, 3, 4, 4.0, 8.0, 100.0) is None
+
+
+def test_cpu_batch_rate_runs_the_oracle_on_a_pool(bench):
+    import pf_inputs as I
+
+    plist = I.batch_manifest()
+    small = [p for p in plist if p["n"][0] <= 64][:2]
+    assert len(small) == 2
+    v, cores, desc = bench.cpu_batch_rate(small, steps=1, max_n=64)
+    assert v > 0 and 1 <= cores <= 2 and "spawned" in desc

@@ -29,7 +29,8 @@ import time
 
 CANDIDATES = tuple(
     [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (1, 2) for c in (1024, 4096, 16384)]
-    + [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (3, 4, 6) for c in (4096, 16384)])
+    + [{"mg_coarse_cells": c, "mg_pre": v, "mg_post": v} for v in (3, 4, 6) for c in (4096, 16384)]
+    + [{"mg_coarse_cells": 4096, "mg_pre": v, "mg_post": v} for v in (8, 10)])
 
 INNER_TOLS = (1e-6, 1e-5, 1e-4, 1e-3)   # the first is the library's default
 

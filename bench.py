@@ -185,6 +185,8 @@ class ClockSampler:
 # by the cell count. Valid for the kernel as profiled; None for every other
 # class.
 NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 13.2}
+NCU_TRAFFIC_NOTE = ("ncu DRAM bytes per cell of a 256^3 capture scaled to this grid by the cell "
+                    "count: a lower bound (at 256^3 part of the reads hit the 129 MB L2)")
 
 
 def deal(items, rank, world):
@@ -420,6 +422,55 @@ def run_batch(args, rank, world, local_rank):
             "cpu_baseline": cpu, "clocks": clk}), flush=True)
 
 
+def fp64_baseline(pf, torch, p, stream, local_rank, graph, steps=3):
+    """The plain float64 GPU path on the same drop at the float64 accuracy
+    (poisson_rtol 1e-12): one untimed step (graph capture), then `steps` timed
+    steps with CUDA events and sampled clocks. Beside it, the mixed path runs
+    the same 1 + steps steps from the same initial phase field (its float32
+    values), and the per-field max-norm distance of the two results, relative
+    to the float64 field's maximum, is reported."""
+    use_graph = 1 if graph else 0
+    with torch.cuda.stream(stream):
+        mix = pf.Simulation(dict(p, use_graph=use_graph), stream=stream)
+    phi0 = mix.field("phi")
+    mix.step(1 + steps)
+    mfields = {c: mix.field(c) for c in ("phi", "u", "v", "w", "p")}
+    mix.close()
+    del mix
+    torch.cuda.empty_cache()
+    q = dict(p, precision="fp64", poisson_rtol=1e-12, use_graph=use_graph)
+    with torch.cuda.stream(stream):
+        sim = pf.Simulation(q, phi0=phi0, stream=stream)
+    sim.step(1)
+    clocks = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    diag = sim.diagnostics()
+    dist = {}
+    for c, mv in mfields.items():
+        fv = sim.field(c)
+        dist[c] = float(np.max(np.abs(mv - fv)) / max(float(np.max(np.abs(fv))), 1e-300))
+    ncell = sim.ncell
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return {"value": ncell * steps / (ms / 1e3) / 1e6, "unit": UNIT,
+            "ms_per_step": ms / steps, "steps": steps, "poisson_rtol": 1e-12,
+            "poisson_relres_last": diag["poisson_relres"], "dtype": "f64",
+            "execution": "one replayed CUDA graph per step" if graph else "host-driven",
+            "clocks": clk,
+            "mixed_vs_fp64_after_steps": 1 + steps,
+            "mixed_vs_fp64_rel_maxnorm": dist}
+
+
 def run_ours(args, rank, world, local_rank):
     """Timed steps of one grid per rank. With graph mode (the default) the
     headline number comes from replayed step graphs; the per-kernel CUDA-event
@@ -516,6 +567,7 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": (NCU_TRAFFIC_PER_CELL[dom] * ncell
                             if dom in NCU_TRAFFIC_PER_CELL and p["dim"] == 3
                             and p.get("precision") == "mixed" else None),
+                "traffic_note": (NCU_TRAFFIC_NOTE if dom in NCU_TRAFFIC_PER_CELL else None),
                 "algo_bytes_per_launch": bpc * ncell,
                 "avg_launch_us": avg_s * 1e6,
                 "share_of_step": dom_ms / ms_h if ms_h > 0 else None,
@@ -559,6 +611,14 @@ def run_ours(args, rank, world, local_rank):
         v, cores, sdesc = cpu_sample_rate(p, steps=6)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
 
+    fp64 = None
+    if rank == 0 and world == 1 and args.fp64 and p["precision"] == "mixed":
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        fp64 = fp64_baseline(pf, torch, p, stream, local_rank, args.graph)
+        sim = None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -585,9 +645,11 @@ def run_ours(args, rank, world, local_rank):
             "poisson_relres_last": diag["poisson_relres"],
             "kernel_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0] > 0},
             "kernel_launches": {k: v[0] for k, v in prof.items() if v[0] > 0},
+            "fp64_baseline": fp64,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -611,6 +673,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=1,
                     help="1 (default): tune the multigrid launch shape (per grid size for the "
                          "batch) before the timed region")
+    ap.add_argument("--fp64", type=int, default=1,
+                    help="1 (default, mixed workloads, one GPU): also time the plain FP64 "
+                         "GPU path on the same grid and report the mixed result's distance")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -54,7 +54,7 @@ typedef enum {
     PF_ERR_NOT_CONVERGED = 3,  /* Poisson solve hit poisson_maxit before poisson_rtol */
     PF_ERR_NONFINITE = 4,      /* NaN or Inf found in the state */
     PF_ERR_UNBOUNDED = 5,      /* phi left [-bound_tol, 1 + bound_tol] (when checked) */
-    PF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+    PF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up (TMA-staged sweeps) */
     PF_ERR_WORKSPACE = 7       /* workspace pointer misaligned or too small */
 } pf_status;
 
@@ -209,10 +209,10 @@ pf_status pf_profile_enable(pf_ctx* ctx, int enable);
 int pf_profile_read(pf_ctx* ctx, pf_profile_entry* out, int max_entries, int reset);
 
 /* Allocation-free pressure solve, for callers that cannot allocate device
- * memory: code that runs where cudaMalloc is forbidden or unsafe (inside a
- * region being captured into a CUDA graph by another library, under a host
- * framework whose memory pool owns all device memory, or after start-up in a
- * real-time loop that must not allocate). It solves the same system as
+ * memory: a host framework whose memory pool owns all device memory (a
+ * cudaMalloc of its own would fail or fragment that pool), or a real-time
+ * loop that must not allocate after start-up (an allocation may synchronise
+ * the device and take unbounded time). It solves the same system as
  * pf_poisson_solve, -div(grad x / rho(phi)) = rhs with the mean of rhs
  * removed and x returned with zero mean, without a context or workspace: all
  * scratch lives in one fixed array inside the library of

@@ -37,14 +37,17 @@ INNER_TOLS = (1e-6, 1e-5, 1e-4, 1e-3)   # the first is the library's default
 _cache: dict = {}
 
 
-def signature(p: dict) -> str:
+def signature(p: dict, tune_inner: bool = False) -> str:
     """What the best launch shape depends on: the grid, precision, model,
-    force, density ratio, walls and execution mode."""
+    force, density ratio, walls, execution mode, the solve's tolerances (a
+    tight poisson_rtol favours stronger V-cycles; a preset inner_tol is part of
+    the problem) and whether the inner tolerance was tuned as well."""
     n = tuple(int(v) for v in p["n"])
     ratio = round(float(p["rho_in"]) / float(p["rho_out"]), 6)
     return json.dumps([int(p["dim"]), n, str(p.get("precision")), str(p.get("model")),
                        str(p.get("force")), ratio, int(p.get("wall_y", 0) or 0),
-                       int(p.get("use_graph", 0) or 0)])
+                       int(p.get("use_graph", 0) or 0), float(p.get("poisson_rtol", 0.0) or 0.0),
+                       float(p.get("inner_tol", 0.0) or 0.0), bool(tune_inner)])
 
 
 def _time_candidate(pf, p: dict, cand: dict, steps: int, warm: int) -> float:
@@ -64,7 +67,7 @@ def tune(p: dict, candidates=CANDIDATES, steps: int = 2, warm: int = 1,
     {candidate: ms}, "cached": bool}."""
     import paper_2205_05835_gb300 as pf
 
-    key = signature(p)
+    key = signature(p, tune_inner)
     if key not in _cache and cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             _cache.update(json.load(f))

@@ -1,6 +1,7 @@
 // C ABI (include/pf.h) and the host-side orchestration of one fractional step:
 // workspace layout, projected RK4 / forward Euler stage sequence, the
 // multigrid-preconditioned CG loop, diagnostics and state transfer.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -1412,14 +1413,17 @@ Impl* make_impl(const pf_params& p, cudaStream_t s, std::string& err) {
 static __device__ __align__(256) unsigned char g_pf_static_scratch[PF_STATIC_SCRATCH_BYTES];
 
 // Device address of the array per device, looked up once per device with that
-// device current (the host-side symbol is only a stand-in for it).
-void* g_static_scratch_addr[64] = {};
+// device current (the host-side symbol is only a stand-in for it). Host
+// threads making their first calls at once may each look it up; they store
+// the same address, and the atomics keep those stores well defined.
+std::atomic<void*> g_static_scratch_addr[64] = {};
 
 template <typename T, int DIM>
 pf_status run_static_solve(const pf_params& prm, cudaStream_t st, void* scratch,
                            const double* phi, const double* rhs, double* x, int* iters,
                            double* relres, std::string& err) {
     ImplT<T, DIM> im(prm, st, err);
+    if (!err.empty()) return PF_ERR_INVALID;
     Carver size_cv{nullptr};
     im.carve_solver_only(size_cv);
     if (size_cv.off > (size_t)PF_STATIC_SCRATCH_BYTES) {
@@ -1465,16 +1469,15 @@ pf_status pf_poisson_solve_static(const pf_params* prm, const double* phi, const
         g_init_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
         return PF_ERR_CUDA;
     }
-    if (!g_static_scratch_addr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_pf_static_scratch);
-        if (e != cudaSuccess || !ptr) {
+    void* scratch = g_static_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
+        e = cudaGetSymbolAddress(&scratch, g_pf_static_scratch);
+        if (e != cudaSuccess || !scratch) {
             g_init_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return PF_ERR_CUDA;
         }
-        g_static_scratch_addr[dev] = ptr;
+        g_static_scratch_addr[dev].store(scratch, std::memory_order_release);
     }
-    void* scratch = g_static_scratch_addr[dev];
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::string err;
     const bool mixed = prm->precision == PF_MIXED;

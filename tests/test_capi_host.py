@@ -223,8 +223,11 @@ def test_mg_coarse_cells_validation_and_autotune_keys(pf):
     a = I.small_case(dim=2, n=64)
     assert autotune.signature(a) == autotune.signature(dict(a, sigma=3.0, R=0.2))
     for other in (dict(n=(80, 80, 1)), dict(precision="mixed"), dict(rho_out=0.01),
-                  dict(use_graph=1), dict(force="csf")):
+                  dict(use_graph=1), dict(force="csf"), dict(poisson_rtol=1e-8),
+                  dict(inner_tol=1e-4)):
         assert autotune.signature(dict(a, **other)) != autotune.signature(a)
+    # a shape tuned without the inner tolerance is not reused when it is asked for
+    assert autotune.signature(a, tune_inner=True) != autotune.signature(a)
     assert {"mg_coarse_cells": 16384, "mg_pre": 1, "mg_post": 1} in autotune.CANDIDATES
     tuned = autotune.apply(a, {"choice": autotune.CANDIDATES[2]})
     assert tuned["mg_coarse_cells"] == 16384 and tuned["sigma"] == a["sigma"]

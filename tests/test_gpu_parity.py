@@ -338,3 +338,48 @@ def test_poisson_mixed_3d_two_sweeps_per_level(pf):
     assert it <= 12, it
     res = O.apply_poisson(beta_f32(phi, g, po), x, g) - rhs
     assert np.linalg.norm(res) <= 2e-12 * np.linalg.norm(rhs)
+
+
+def test_unbounded_phi_is_reported(pf):
+    """bound_tol > 0: a phase field outside [-bound_tol, 1 + bound_tol] (one cell
+    at 1.2, prepared on the host) is reported as PF_ERR_UNBOUNDED, and the same
+    field passes when the check is off."""
+    p = I.small_case(dim=2, n=32, bound_tol=1e-3)
+    po = O.params_from(p)
+    phi = O.initial_phi(po)
+    phi[7, 9] = 1.2
+    sim = pf.Simulation(p, phi0=phi)
+    with pytest.raises(pf.PFError) as e:
+        sim.diagnostics()
+    assert e.value.status == pf.B.PF_ERR_UNBOUNDED
+    sim.close()
+    sim = pf.Simulation(dict(p, bound_tol=0.0), phi0=phi)
+    assert sim.diagnostics()["phi_max"] == pytest.approx(1.2)
+    sim.close()
+
+
+@pytest.mark.parametrize("dim,n,precision,tol", [(2, 32, "fp64", 1e-13), (3, 32, "mixed", 2e-6)])
+def test_rk4_shear_mode_amplification_gpu(pf, dim, n, precision, tol):
+    """One GPU step of the divergence-free shear mode u_x = A sin(2 pi k y)
+    (sigma = 0, uniform fluid) multiplies it by the RK4 stability polynomial
+    R(z), z = -nu dt (4/h^2) sin^2(pi k h): the tableau pinned without the
+    oracle (the 3D mixed case runs the column-marching stage kernel)."""
+    import math
+
+    k, nu, amp = 2, 0.05, 0.3
+    p = I.small_case(dim=dim, n=n, sigma=0.0, rho_in=1.0, rho_out=1.0, mu_in=nu, mu_out=nu,
+                     pert_mode=0, pert_amp=0.0, precision=precision)
+    g = O.Grid(dim, p["n"], p["L"])
+    lam = 4.0 / g.h ** 2 * math.sin(math.pi * k * g.h) ** 2
+    p["dt"] = 0.5 / (nu * lam)
+    z = -0.5
+    y = g.centres()[1]
+    u0 = amp * np.sin(2.0 * math.pi * k * y)
+    sim = pf.Simulation(p, phi0=np.zeros(g.shape))
+    sim.set_field("u", u0)
+    u0 = sim.field("u")          # as stored (float32 in the mixed path)
+    sim.step(1)
+    R = 1.0 + z + z * z / 2.0 + z ** 3 / 6.0 + z ** 4 / 24.0
+    assert np.max(np.abs(sim.field("u") - R * u0)) <= tol * amp
+    assert np.max(np.abs(sim.field("v"))) <= tol * amp
+    sim.close()

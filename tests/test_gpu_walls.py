@@ -99,17 +99,25 @@ def test_wall_conditions_on_gpu(pf, precision):
 
 
 def test_walled_mixed_against_fp64(pf):
-    """Mixed precision after 100 steps of the 64^2 wave: stated bounds
-    phi < 1e-5, u, v < 1e-3, p < 1e-3 (max-norm relative; measured 1.4e-6,
-    2e-4, 1.1e-4)."""
+    """Mixed precision against float64 on the 64^2 wave, max-norm relative.
+    After 5 steps the drops' bounds hold (phi < 1e-5, u, v < 2e-3, p < 1e-4).
+    The distance grows with the step count (float32 storage of phi and u
+    rounds every step), so after 100 steps the stated bounds are phi < 1e-5,
+    u, v < 1e-3 and p < 2e-4 (measured after 100 steps: 1.4e-6, 2e-4 and
+    1.1e-4)."""
     a = pf.Simulation(I.standing_wave(n=64, precision="fp64"))
     b = pf.Simulation(I.standing_wave(n=64, precision="mixed"))
-    a.step(100)
-    b.step(100)
+    a.step(5)
+    b.step(5)
+    e5 = {c: rel(b.field(c), a.field(c)) for c in ("phi", "u", "v", "p")}
+    a.step(95)
+    b.step(95)
     errs = {c: rel(b.field(c), a.field(c)) for c in ("phi", "u", "v", "p")}
+    print("walled mixed vs fp64: 5 steps", e5, "100 steps", errs)
+    assert e5["phi"] < 1e-5 and max(e5["u"], e5["v"]) < 2e-3 and e5["p"] < 1e-4, e5
     assert errs["phi"] < 1e-5, errs
     assert errs["u"] < 1e-3 and errs["v"] < 1e-3, errs
-    assert errs["p"] < 1e-3, errs
+    assert errs["p"] < 2e-4, errs
     a.close()
     b.close()
 

@@ -1,14 +1,14 @@
 """The allocation-free pressure solve (pf_poisson_solve_static).
 
-Some callers cannot allocate device memory: code that runs inside another
-library's CUDA-graph capture, under a framework whose memory pool owns all
-device memory, or in a real-time loop that must not allocate after start-up.
-pf_poisson_solve_static serves them with scratch in a fixed array inside the
-library. This file checks, through the C ABI, that two calls in a row give the
-same solution as the context-based pf_poisson_solve, within the tolerance the
-other Poisson tests use, and that grids beyond the array's capacity are
-rejected with a clear error. It is collected last so that a failure here
-leaves every other test already run; it passes alone in a fresh process too.
+Some callers cannot allocate device memory: a framework whose memory pool
+owns all device memory, or a real-time loop that must not allocate after
+start-up. pf_poisson_solve_static serves them with scratch in a fixed array
+inside the library. This file checks, through the C ABI, that two calls in a
+row give the same solution as the context-based pf_poisson_solve, within the
+tolerance the other Poisson tests use, and as the oracle's exact solve; and
+that grids beyond the array's capacity are rejected with a clear error. It is
+collected last so that a failure here leaves every other test already run; it
+passes alone in a fresh process too.
 """
 import numpy as np
 import pytest
@@ -31,6 +31,16 @@ def env():
     import paper_2205_05835_gb300 as pf
 
     return pf, torch
+
+
+def beta_f32(phi, g, p):
+    """1 / rho_f evaluated and rounded in float32 from float32 phi, as float64."""
+    ph = phi.astype(np.float32)
+    c = np.clip(ph, np.float32(0), np.float32(1))
+    dr = np.float32(np.float32(p["rho_in"]) - np.float32(p["rho_out"]))
+    rho = np.float32(p["rho_out"]) + (dr * c).astype(np.float32)
+    return [(np.float32(1) / (np.float32(0.5) * (rho + np.roll(rho, 1, axis=g.axis(d)))))
+            .astype(np.float64) for d in range(g.dim)]
 
 
 @pytest.mark.parametrize("dim,n,precision,tol", [(3, 32, "fp64", 1e-9), (2, 96, "fp64", 1e-9),
@@ -63,6 +73,12 @@ def test_static_solve_matches_context_solve(env, dim, n, precision, tol):
         got = d_x.cpu().numpy().reshape(g.shape)
         err = np.max(np.abs(got - want)) / np.max(np.abs(want))
         assert err < tol, (call, err)
+    # and the oracle's exact solve of the same system (the mixed path's
+    # operator has float32-rounded face coefficients of float32 phi)
+    beta = O.face_beta(phi, g, po) if precision == "fp64" else beta_f32(phi, g, po)
+    exact = O.solve_poisson(beta, rhs, g)
+    err = np.max(np.abs(got - exact)) / np.max(np.abs(exact))
+    assert err < tol, err
 
 
 def test_static_solve_rejects_oversized_grids(env):

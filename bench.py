@@ -493,6 +493,8 @@ def run_ours(args, rank, world, local_rank):
         p["inner_tol"] = args.inner_tol
     if args.mg_sweeps is not None:
         p["mg_pre"] = p["mg_post"] = args.mg_sweeps
+    if args.sweep_staging is not None:
+        p["sweep_staging"] = args.sweep_staging
     tuned = None
     if args.autotune and args.mg_sweeps is None:
         # multigrid launch shape tuned on this grid before the timed region
@@ -667,6 +669,8 @@ def main():
                     help="relative reduction of each float32 inner solve (mixed path)")
     ap.add_argument("--mg-sweeps", type=int, default=None,
                     help="pre- and post-smoothing sweeps per V-cycle (tuning; default 1)")
+    ap.add_argument("--sweep-staging", type=int, default=None,
+                    help="finest-level sweeps: 0 TMA-staged (the library's default), 1 cp.async")
     ap.add_argument("--graph", type=int, default=1,
                     help="1 (default): replay one captured CUDA graph per step (use_graph); "
                          "0: host-driven solver loops")

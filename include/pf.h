@@ -120,7 +120,12 @@ typedef struct {
                              one single-CTA V-cycle kernel (0: 4096; else 16 .. 2^20). A
                              tuning knob: it changes the preconditioner, not the converged
                              solution (see the package's autotune module) */
-    int reserved[3];      /* must be zero */
+    int sweep_staging;    /* finest-level red-black sweeps of the 3D mixed path: 0 (default)
+                             planes staged into shared memory by the Tensor Memory Accelerator
+                             (tensor and bulk copies completing on mbarriers) where the grid
+                             allows (n[0] % 4 == 0, n[0] >= 40); 1: by per-thread cp.async
+                             chunks. Same arithmetic, same results. */
+    int reserved[2];      /* must be zero */
 } pf_params;
 
 typedef struct {

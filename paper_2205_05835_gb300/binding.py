@@ -52,7 +52,8 @@ class pf_params(ctypes.Structure):
         ("wall_y", ctypes.c_int),
         ("shape", ctypes.c_int),
         ("mg_coarse_cells", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("sweep_staging", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 

@@ -201,7 +201,11 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "mg_coarse_cells must be 0 or in 16 .. 2^20";
         return PF_ERR_INVALID;
     }
-    for (int i = 0; i < 3; ++i)
+    if (p->sweep_staging != 0 && p->sweep_staging != 1) {
+        why = "sweep_staging must be 0 or 1";
+        return PF_ERR_INVALID;
+    }
+    for (int i = 0; i < 2; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
     return PF_OK;
 }
@@ -317,7 +321,10 @@ struct ImplT final : Impl {
     bool owns_host = false;
     cudaEvent_t sleep_ev = nullptr;   // blocking-sync event (batched execution)
 
+    SweepTMA* tma = nullptr;   // tensor maps of the TMA-staged finest sweep (host object)
+
     ~ImplT() override {
+        if (tma) sweep_tma_destroy(tma);
         if (gexec) cudaGraphExecDestroy(gexec);
         prof.destroy();
         if (sleep_ev) cudaEventDestroy(sleep_ev);
@@ -526,6 +533,15 @@ struct ImplT final : Impl {
         CK(cudaMemcpyAsync(sc, h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(gamma, 0, sizeof(double), st));
         CK(cudaStreamSynchronize(st));
+        // finest-level sweeps staged by the TMA (3D mixed path; the rest of the
+        // hierarchy keeps the cp.async sweeps)
+        if (DIM == 3 && sizeof(T) == sizeof(float) && rho0 != nullptr && H.lev[0].x2 != nullptr &&
+            prm.sweep_staging == 0 && H.first_coarse > 0) {
+            tma = sweep_tma_create(g, rho0, reinterpret_cast<const float*>(H.lev[0].f),
+                                   reinterpret_cast<const float*>(H.lev[0].x),
+                                   reinterpret_cast<const float*>(H.lev[0].x2));
+            H.tma = tma;
+        }
         return PF_OK;
     }
 
@@ -697,7 +713,9 @@ struct ImplT final : Impl {
             h_sc->status = 0;
             CK(cudaMemsetAsync(&sc->status, 0, sizeof(int), st));
             err = stt == PF_ERR_NOT_CONVERGED ? "Poisson solve reached poisson_maxit"
-                                              : "non-finite value in the Poisson solve";
+                  : stt == PF_ERR_TIMEOUT
+                      ? "a bounded wait of the TMA-staged sweep gave up (copies did not land)"
+                      : "non-finite value in the Poisson solve";
             return (pf_status)stt;
         }
         return PF_OK;
@@ -761,6 +779,7 @@ struct ImplT final : Impl {
     // such call runs inside the capture).
     pf_status capture_step() {
         sweep3d_prepare();
+        sweep_tma_prepare();
         coarse_prepare();
         // the legacy default stream cannot be captured: record on a private
         // stream (recording runs nothing); the graph replays on the context's

@@ -125,10 +125,15 @@ struct MGLevel {
 
 
 
+// TMA-staged finest-level sweep (pf_sweep_tma.cu): tensor maps of the level-0
+// arrays of one context.
+struct SweepTMA;
+
 template <typename T>
 struct MGHier {
     const float* rho0 = nullptr;   // float32 cell densities of level 0 (3D mixed path), formed
                                    // once per solve; the finest sweep reads them instead of phi
+    const SweepTMA* tma = nullptr; // level 0 sweeps staged by the TMA (nullptr: cp.async)
     int nlev;
     int first_coarse;   // levels >= first_coarse are handled by one single-CTA kernel
     int pre, post;
@@ -159,6 +164,19 @@ struct SweepDots {
     CGScalars* sc;
     int first;
 };
+// The finest-level sweep staged by the TMA: eligible grids, tensor maps of
+// the cell densities rho, the right-hand side f and the two correction buffers
+// of level 0 (host object, nullptr when not eligible or the driver lacks the
+// encoder), and the launch (false: not launched, use launch_sweep3d). A
+// bounded wait that gives up latches PF_ERR_TIMEOUT in the solve's scalars.
+bool sweep_tma_ok(const Dims& g);
+SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, const float* xa,
+                           const float* xb);
+void sweep_tma_destroy(SweepTMA* t);
+void sweep_tma_prepare();
+bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* xin, float* xout,
+                      const SweepDots* dots, int first_color, const CGScalars* sc,
+                      cudaStream_t s);
 // CG direction update and operator product (3D float32, face arrays).
 bool dir3d_ok(const Dims& g);
 void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,

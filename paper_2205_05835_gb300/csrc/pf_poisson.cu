@@ -530,10 +530,13 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                 T* oth = L.x2;
                 for (int p = 0; p < H.pre; ++p) {
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
-                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L), l == 0 ? phi0 : nullptr,
-                                   rho_ready, ph,
-                                   p == 0 ? nullptr : reinterpret_cast<const float*>(cur),
-                                   reinterpret_cast<float*>(p == 0 ? cur : oth), nullptr, 0, sc, s);
+                    const float* xin = p == 0 ? nullptr : reinterpret_cast<const float*>(cur);
+                    float* xout = reinterpret_cast<float*>(p == 0 ? cur : oth);
+                    if (!(l == 0 && launch_sweep_tma(H.tma, reinterpret_cast<const MGLevel<float>&>(L),
+                                                     xin, xout, nullptr, 0, sc, s)))
+                        launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
+                                       l == 0 ? phi0 : nullptr, rho_ready, ph, xin, xout, nullptr, 0,
+                                       sc, s);
                     pr->end();
                     if (p > 0) { T* t = cur; cur = oth; oth = t; }
                 }
@@ -590,10 +593,13 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                     const bool fuse = dots && l == 0 && p == H.post - 1 &&
                                       2 * sweep3d_blocks(L.g) <= kRedPart;
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
-                    launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L), l == 0 ? phi0 : nullptr,
-                                   rho_ready, ph,
-                                   reinterpret_cast<const float*>(cur), reinterpret_cast<float*>(oth),
-                                   fuse ? dots : nullptr, 1, sc, s);
+                    const float* xin = reinterpret_cast<const float*>(cur);
+                    float* xout = reinterpret_cast<float*>(oth);
+                    if (!(l == 0 && launch_sweep_tma(H.tma, reinterpret_cast<const MGLevel<float>&>(L),
+                                                     xin, xout, fuse ? dots : nullptr, 1, sc, s)))
+                        launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
+                                       l == 0 ? phi0 : nullptr, rho_ready, ph, xin, xout,
+                                       fuse ? dots : nullptr, 1, sc, s);
                     pr->end();
                     if (fuse && dots_done) *dots_done = true;
                     T* t = cur; cur = oth; oth = t;

@@ -65,7 +65,11 @@ def test_workspace_size_and_validation(pf):
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
     bad = pf.make_params(I.static_drop_64())
-    bad.reserved[2] = 1
+    bad.reserved[1] = 1
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(bad)
+    bad = pf.make_params(I.static_drop_64())
+    bad.sweep_staging = 2
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
 

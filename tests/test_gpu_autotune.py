@@ -54,7 +54,7 @@ def test_tune_picks_a_candidate_and_caches(pf):
     assert r["choice"].get("inner_tol", 1e-6) in autotune.INNER_TOLS
     assert len(r["ms_per_step"]) == len(autotune.CANDIDATES) + len(autotune.INNER_TOLS) - 1
     assert all(v > 0 for v in r["ms_per_step"].values())
-    assert autotune.tune(p)["cached"]
+    assert autotune.tune(p, tune_inner=True)["cached"]
     sim = pf.Simulation(autotune.apply(p, r))
     sim.step(3)
     assert sim.diagnostics()["poisson_relres"] < 1e-10

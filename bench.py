@@ -208,13 +208,17 @@ def job_time(seconds, dist=None, device=None):
 
 def algo_bytes_per_cell(cls, dim, w):
     d = dim
+    # the 3D float32 path forms the CG operator's and the finest restriction's
+    # coefficients from the cell densities (one array) instead of d face arrays
+    ncoef = 1 if (dim == 3 and w == 4) else d
     table = {
         # one full red-black sweep of the finest level (weights from phi), mean
         # of the pre-smoothing sweep (zero start: read f, phi; write x) and the
         # post-smoothing sweep (read x, f, phi, and q for the fused dots; write x)
         "mg_gs_level0": 0.5 * (3 * w + 5 * w),
-        # p = z + beta p, q = A p: read z, p, 3 face arrays; write p, q
-        "cg_dir_spmv": (2 + d + 2) * w,
+        # p = z + beta p, q = A p: read z, p and the coefficients (cell densities
+        # or d face arrays); write p, q
+        "cg_dir_spmv": (2 + ncoef + 2) * w,
         # e += a p, r -= a q: read e, p, r, q; write e, r
         "cg_update": 6 * w,
         # r.z, z.q: read z, r, q
@@ -228,7 +232,7 @@ def algo_bytes_per_cell(cls, dim, w):
         "cell_pass": w + (d + 1) * w,
         "correct": d * w + 8 + d * w + d * w,
         "divergence": d * w + 8,
-        "mg_restrict": (2 + d) * w + w / (2 ** d),
+        "mg_restrict": (2 + ncoef) * w + w / (2 ** d),
         "mg_prolong": 2 * w + w / (2 ** d),
         # float32 face coefficients (and cell densities) from phi
         "beta0_f64": w + d * w + w,

@@ -634,7 +634,7 @@ struct ImplT final : Impl {
             launch_dir3d_reg(g, reinterpret_cast<const float*>(io.z),
                              reinterpret_cast<const float*>(cur ? pd[1] : pd[0]),
                              reinterpret_cast<float*>(cur ? pd[0] : pd[1]),
-                             reinterpret_cast<float*>(qT), bl, first, rb, sc, st);
+                             reinterpret_cast<float*>(qT), bl, rho0, first, rb, sc, st);
         } else {
             launch_in_dir<T, DIM>(g, ph, io, cur, first, rb, sc, st);
         }

@@ -179,9 +179,11 @@ bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* x
                       cudaStream_t s);
 // CG direction update and operator product (3D float32, face arrays).
 bool dir3d_ok(const Dims& g);
+// rho != nullptr: coefficients 2 / (rho_c + rho_q) from the cell densities
+// (hardware reciprocal) instead of the face arrays.
 void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
-                      const float* const* beta, int first, RedBuf rb, CGScalars* sc,
-                      cudaStream_t s);
+                      const float* const* beta, const float* rho, int first, RedBuf rb,
+                      CGScalars* sc, cudaStream_t s);
 // Float64-accurate outer residual r = sign (b - mean b) - A x of the mixed 3D
 // path (x, b double-floats: n hi parts then n lo parts; r float32), one thread
 // per column marching in z; also ||f||^2 (first) and ||r||^2 and the solve's
@@ -193,8 +195,10 @@ void launch_ir_residual3d(const Dims& g, const float* x, const float* b, const f
 // Restriction (mean of the children's residual) from a 3D float32 level with
 // face arrays and even sizes to the next coarser level.
 bool restrict3d_ok(const Dims& fine);
-void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const CGScalars* sc,
-                       cudaStream_t s);
+// rho != nullptr (finest level): weights 2 / (rho_c + rho_q) from the cell
+// densities instead of the level's face arrays.
+void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const float* rho,
+                       const CGScalars* sc, cudaStream_t s);
 // Column-marching per-stage kernels for 3D float32 grids (pf_stage3d.cu).
 void launch_cell_pass_mu3d(const Dims& g, const Phys& ph, const float* phi, float* n0, float* n1,
                            float* n2, float* mu, cudaStream_t s);

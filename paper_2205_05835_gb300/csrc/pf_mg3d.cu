@@ -477,10 +477,19 @@ bool dir3d_ok(const Dims& g) {
 
 // ---------------------------------------------------------------------------
 // CG search direction and operator product on 3D float32 grids:
-//   p_new = z + beta p_old ; q = A p_new ; alpha = rz / (p_new . q)
-// Register z-march: one thread per column of a 32 x 8 tile; p_new of the column at k-1, k, k+1 and the z-face
-// coefficient above are carried in registers, the in-plane neighbours come
-// through L1. No shared memory and no barriers.
+//   p_new = z + beta p_old ; q = A' p_new ; alpha = rz / (p_new . q)
+// Register z-march: one thread per column of a 32 x 8 tile; p_new of the
+// column at k-1, k, k+1 and the z-face coefficient above are carried in
+// registers, the in-plane neighbours come through L1. No shared memory and no
+// barriers.
+//
+// The face coefficients come either from the three face arrays (A' = A, the
+// float32 operator of the outer residual) or from the cell densities as
+// 2 / (rho_c + rho_q) with the hardware reciprocal (RHO): one array instead of
+// three, 8 fewer bytes per cell. The inner CG then solves with A' = A up to
+// the reciprocal's rounding (about 2^-22 relative per coefficient); the
+// float64 refinement around it forms every residual with A, so the converged
+// pressure is that of A all the same.
 // ---------------------------------------------------------------------------
 namespace pf {
 namespace {
@@ -494,6 +503,7 @@ struct DirRegArgs {
     const float* bx;
     const float* by;
     const float* bz;
+    const float* rho;
     float ih2;
     int first;
     int zc;
@@ -501,6 +511,13 @@ struct DirRegArgs {
     CGScalars* sc;
 };
 
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <bool RHO>
 __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
     CGScalars* sc = A.sc;
     if (sc->done || sc->idone) return;
@@ -523,6 +540,7 @@ __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
         const float* __restrict__ bxp = A.bx;
         const float* __restrict__ byp = A.by;
         const float* __restrict__ bzp = A.bz;
+        const float* __restrict__ rp = A.rho;
         float* __restrict__ pnew = A.p_new;
         float* __restrict__ qo = A.q;
         const bool first = first_it != 0;
@@ -533,11 +551,19 @@ __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
         const int km1 = z0 == 0 ? g.nz - 1 : z0 - 1;
         float p_m = pn(km1 * sz + col);
         float p_c = pn(z0 * sz + col);
-        float bz_c = __ldg(bzp + z0 * sz + col);
+        // z-face coefficient below plane k; RHO: also rho of plane k
+        float r_c = 0.f, bz_c;
+        if (RHO) {
+            r_c = __ldg(rp + z0 * sz + col);
+            bz_c = rcp_fast(r_c + __ldg(rp + km1 * sz + col));
+        } else {
+            bz_c = __ldg(bzp + z0 * sz + col);
+        }
         // the loads of plane k: in-plane neighbours of p_new (as z, p_old), the
-        // x / y face coefficients, and the centre of plane k + 1 with its z face
+        // x / y face coefficients (RHO: the neighbours' densities), and the
+        // centre of plane k + 1 with its z face (RHO: its density)
         struct Ld {
-            float z[4], p[4], bx0, bx1, by0, by1, zn, pnx, bzn;
+            float z[4], p[4], c[4], zn, pnx, bzn;
         };
         auto load = [&](int k, Ld& L) {
             const int idx = k * sz + col;
@@ -548,29 +574,46 @@ __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
                 L.z[q] = __ldg(zp + o[q]);
                 L.p[q] = first ? 0.f : __ldg(po + o[q]);
             }
-            L.bx0 = __ldg(bxp + idx);
-            L.bx1 = __ldg(bxp + idx + ox_p);
-            L.by0 = __ldg(byp + idx);
-            L.by1 = __ldg(byp + idx + oy_p);
+            if (RHO) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) L.c[q] = __ldg(rp + o[q]);
+                L.bzn = __ldg(rp + idxp);
+            } else {
+                L.c[0] = __ldg(bxp + idx);
+                L.c[1] = __ldg(bxp + idx + ox_p);
+                L.c[2] = __ldg(byp + idx);
+                L.c[3] = __ldg(byp + idx + oy_p);
+                L.bzn = __ldg(bzp + idxp);
+            }
             L.zn = __ldg(zp + idxp);
             L.pnx = first ? 0.f : __ldg(po + idxp);
-            L.bzn = __ldg(bzp + idxp);
         };
         auto apply = [&](int k, const Ld& L) {
             const int idx = k * sz + col;
             const float p_p = L.zn + bcg * L.pnx;
-            float nb[4];
+            float nb[4], w[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) nb[q] = L.z[q] + bcg * L.p[q];
-            const float ax = L.bx0 * (p_c - nb[0]) + L.bx1 * (p_c - nb[1]) + L.by0 * (p_c - nb[2]) +
-                             L.by1 * (p_c - nb[3]) + bz_c * (p_c - p_m) + L.bzn * (p_c - p_p);
+            float bz_n;
+            if (RHO) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = rcp_fast(r_c + L.c[q]);
+                bz_n = rcp_fast(r_c + L.bzn);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = L.c[q];
+                bz_n = L.bzn;
+            }
+            const float ax = w[0] * (p_c - nb[0]) + w[1] * (p_c - nb[1]) + w[2] * (p_c - nb[2]) +
+                             w[3] * (p_c - nb[3]) + bz_c * (p_c - p_m) + bz_n * (p_c - p_p);
             const float qv = ax * A.ih2;
             pnew[idx] = p_c;
             qo[idx] = qv;
             pq += p_c * qv;
             p_m = p_c;
             p_c = p_p;
-            bz_c = L.bzn;
+            bz_c = bz_n;
+            if (RHO) r_c = L.bzn;
         };
         // two planes per round: all loads of both before the arithmetic
         int k = z0;
@@ -600,8 +643,8 @@ __global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
 }  // namespace
 
 void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* p_new, float* q,
-                      const float* const* beta, int first, RedBuf rb, CGScalars* sc,
-                      cudaStream_t s) {
+                      const float* const* beta, const float* rho, int first, RedBuf rb,
+                      CGScalars* sc, cudaStream_t s) {
     DirRegArgs a;
     a.g = g;
     a.z = z;
@@ -611,14 +654,19 @@ void launch_dir3d_reg(const Dims& g, const float* z, const float* p_old, float* 
     a.bx = beta[0];
     a.by = beta[1];
     a.bz = beta[2];
-    a.ih2 = g.ih2f;
+    a.rho = rho;
+    // 1/rho_f = 2 / (rho_c + rho_q): the factor 2 goes with 1/h^2
+    a.ih2 = rho ? 2.f * g.ih2f : g.ih2f;
     a.first = first;
     a.rb = rb;
     a.sc = sc;
     const int zc = tiled_zc(g);
     a.zc = zc;
     dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
-    k_dir3d_reg<<<grid, 256, 0, s>>>(a);
+    if (rho)
+        k_dir3d_reg<true><<<grid, 256, 0, s>>>(a);
+    else
+        k_dir3d_reg<false><<<grid, 256, 0, s>>>(a);
 }
 
 }  // namespace pf
@@ -777,11 +825,14 @@ void launch_ir_residual3d(const Dims& g, const float* x, const float* b, const f
 }  // namespace pf
 
 // ---------------------------------------------------------------------------
-// Restriction on 3D float32 levels with face arrays: f_C(I) = mean over the 8
-// children of the fine residual f - A x. One thread per coarse column (I, J)
-// marching in z; the 2 x 2 fine block of the planes k - 1, k, k + 1 and the
-// z-face coefficients are carried in registers, the in-plane neighbours and
-// coefficients come through L1 as pairs.
+// Restriction on 3D float32 levels: f_C(I) = mean over the 8 children of the
+// fine residual f - A x. One thread per coarse column (I, J) marching in z;
+// the 2 x 2 fine block of the planes k - 1, k, k + 1 and the z-face
+// coefficients are carried in registers, the in-plane neighbours and
+// coefficients come through L1 as pairs. The coefficients come from the
+// level's face arrays, or on the finest level from the cell densities as
+// 2 / (rho_c + rho_q) with the hardware reciprocal (RHO), the weights the
+// finest smoother uses: one array instead of three.
 // ---------------------------------------------------------------------------
 namespace pf {
 namespace {
@@ -793,10 +844,16 @@ struct RestrictArgs {
     const float* bx;
     const float* by;
     const float* bz;
+    const float* rho;
     float* cf;
     int zc;   // coarse planes per CTA
 };
 
+__device__ __forceinline__ float2 rcp2(float2 a, float2 b) {
+    return make_float2(rcp_fast(a.x + b.x), rcp_fast(a.y + b.y));
+}
+
+template <bool RHO>
 __global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CGScalars* sc) {
     if (sc->done || sc->idone) return;
     const int I = blockIdx.x * 32 + threadIdx.x % 32;
@@ -808,12 +865,14 @@ __global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CG
     const int im = i == 0 ? nx - 1 : i - 1, ip2 = i + 2 == nx ? 0 : i + 2;
     const int r0 = j * nx, r1 = r0 + nx;
     const int rs = (j == 0 ? ny - 1 : j - 1) * nx, rn = (j + 2 == ny ? 0 : j + 2) * nx;
-    const float ih2 = g.ih2f;
+    // 1/rho_f = 2 / (rho_c + rho_q): the factor 2 goes with 1/h^2
+    const float ih2 = RHO ? 2.f * g.ih2f : g.ih2f;
     const float* __restrict__ x = A.x;
     const float* __restrict__ f = A.f;
     const float* __restrict__ bx = A.bx;
     const float* __restrict__ by = A.by;
     const float* __restrict__ bz = A.bz;
+    const float* __restrict__ rho = A.rho;
     auto pair = [](const float* a, int o) { return __ldg(reinterpret_cast<const float2*>(a + o)); };
     float* __restrict__ cf = A.cf;
     const int K0 = blockIdx.z * A.zc;
@@ -824,7 +883,17 @@ __global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CG
     const int kbm = (k == 0 ? nz - 1 : k - 1) * sz;
     float2 m0 = pair(x, kbm + r0 + i), m1 = pair(x, kbm + r1 + i);
     float2 c0 = pair(x, kb + r0 + i), c1 = pair(x, kb + r1 + i);
-    float2 zc0 = pair(bz, kb + r0 + i), zc1 = pair(bz, kb + r1 + i);
+    float2 zc0, zc1;
+    float2 rc0 = make_float2(0.f, 0.f), rc1 = rc0;   // RHO: densities of the block in plane k
+    if (RHO) {
+        rc0 = pair(rho, kb + r0 + i);
+        rc1 = pair(rho, kb + r1 + i);
+        zc0 = rcp2(rc0, pair(rho, kbm + r0 + i));
+        zc1 = rcp2(rc1, pair(rho, kbm + r1 + i));
+    } else {
+        zc0 = pair(bz, kb + r0 + i);
+        zc1 = pair(bz, kb + r1 + i);
+    }
     for (int K = K0; K < K1; ++K) {
         float s = 0.f;
 #pragma unroll
@@ -832,16 +901,41 @@ __global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CG
             const int kp = k + 1 == nz ? 0 : k + 1;
             const int kpb = kp * sz;
             const float2 p0 = pair(x, kpb + r0 + i), p1 = pair(x, kpb + r1 + i);
-            const float2 zp0 = pair(bz, kpb + r0 + i), zp1 = pair(bz, kpb + r1 + i);
-            // in-plane neighbours and coefficients of plane k
+            // in-plane neighbours of plane k
             const float xl0 = __ldg(x + kb + r0 + im), xl1 = __ldg(x + kb + r1 + im);
             const float xr0 = __ldg(x + kb + r0 + ip2), xr1 = __ldg(x + kb + r1 + ip2);
             const float2 xs = pair(x, kb + rs + i), xn = pair(x, kb + rn + i);
-            const float2 bx0 = pair(bx, kb + r0 + i), bx1 = pair(bx, kb + r1 + i);
-            const float bxr0 = __ldg(bx + kb + r0 + ip2), bxr1 = __ldg(bx + kb + r1 + ip2);
-            const float2 by0 = pair(by, kb + r0 + i), by1 = pair(by, kb + r1 + i),
-                         by2 = pair(by, kb + rn + i);
             const float2 f0 = pair(f, kb + r0 + i), f1 = pair(f, kb + r1 + i);
+            // face coefficients of plane k: x faces at i, i + 1 (pairs) and
+            // i + 2, y faces at j, j + 1, j + 2 (pairs), z faces above
+            float2 bx0, bx1, by0, by1, by2, zp0, zp1, rp0, rp1;
+            float bxr0, bxr1;
+            if (RHO) {
+                rp0 = pair(rho, kpb + r0 + i);
+                rp1 = pair(rho, kpb + r1 + i);
+                const float rl0 = __ldg(rho + kb + r0 + im), rl1 = __ldg(rho + kb + r1 + im);
+                const float rr0 = __ldg(rho + kb + r0 + ip2), rr1 = __ldg(rho + kb + r1 + ip2);
+                const float2 rsv = pair(rho, kb + rs + i), rnv = pair(rho, kb + rn + i);
+                bx0 = make_float2(rcp_fast(rl0 + rc0.x), rcp_fast(rc0.x + rc0.y));
+                bx1 = make_float2(rcp_fast(rl1 + rc1.x), rcp_fast(rc1.x + rc1.y));
+                bxr0 = rcp_fast(rc0.y + rr0);
+                bxr1 = rcp_fast(rc1.y + rr1);
+                by0 = rcp2(rsv, rc0);
+                by1 = rcp2(rc0, rc1);
+                by2 = rcp2(rc1, rnv);
+                zp0 = rcp2(rc0, rp0);
+                zp1 = rcp2(rc1, rp1);
+            } else {
+                zp0 = pair(bz, kpb + r0 + i);
+                zp1 = pair(bz, kpb + r1 + i);
+                bx0 = pair(bx, kb + r0 + i);
+                bx1 = pair(bx, kb + r1 + i);
+                bxr0 = __ldg(bx + kb + r0 + ip2);
+                bxr1 = __ldg(bx + kb + r1 + ip2);
+                by0 = pair(by, kb + r0 + i);
+                by1 = pair(by, kb + r1 + i);
+                by2 = pair(by, kb + rn + i);
+            }
             // children in the order (x fastest, then y) of the plane
             const float a00 = bx0.x * (c0.x - xl0) + bx0.y * (c0.x - c0.y) +
                               by0.x * (c0.x - xs.x) + by1.x * (c0.x - c1.x) +
@@ -862,6 +956,10 @@ __global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CG
             c1 = p1;
             zc0 = zp0;
             zc1 = zp1;
+            if (RHO) {
+                rc0 = rp0;
+                rc1 = rp1;
+            }
             kb = kpb;
         }
         cf[(K * A.cg.ny + J) * A.cg.nx + I] = 0.125f * s;
@@ -875,9 +973,10 @@ bool restrict3d_ok(const Dims& fine) {
            fine.nx >= 4 && fine.ny >= 4 && fine.nz >= 4;
 }
 
-void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const CGScalars* sc,
-                       cudaStream_t s) {
+void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const float* rho,
+                       const CGScalars* sc, cudaStream_t s) {
     RestrictArgs a;
+    a.rho = rho;
     a.fg = F.g;
     a.cg = C.g;
     a.x = F.x;
@@ -891,7 +990,10 @@ void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const C
     while (zc > 1 && (long long)cols * ((C.g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
     a.zc = zc;
     dim3 grid((C.g.nx + 31) / 32, (C.g.ny + 7) / 8, (C.g.nz + zc - 1) / zc);
-    k_restrict3d_reg<<<grid, 256, 0, s>>>(a, sc);
+    if (rho)
+        k_restrict3d_reg<true><<<grid, 256, 0, s>>>(a, sc);
+    else
+        k_restrict3d_reg<false><<<grid, 256, 0, s>>>(a, sc);
 }
 
 }  // namespace pf

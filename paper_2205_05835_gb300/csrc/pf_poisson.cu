@@ -555,7 +555,8 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
         if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
             if (L.beta[0] != nullptr && restrict3d_ok(L.g)) {
                 launch_restrict3d(reinterpret_cast<const MGLevel<float>&>(L),
-                                  reinterpret_cast<const MGLevel<float>&>(H.lev[l + 1]), sc, s);
+                                  reinterpret_cast<const MGLevel<float>&>(H.lev[l + 1]),
+                                  l == 0 ? H.rho0 : nullptr, sc, s);
                 done_r = true;
             }
         }

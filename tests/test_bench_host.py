@@ -17,10 +17,14 @@ def bench():
 
 
 def test_step_roofline_sums_finest_classes(bench):
-    # two classes on a 1000-cell grid: 16 B/cell x 10 launches and 28 B/cell x 5
+    # two classes on a 1000-cell 3D float32 grid: 16 B/cell x 10 launches and
+    # 20 B/cell x 5 (the direction product reads the cell densities, not the
+    # three face arrays: 28 B/cell in float32 with face arrays, 2D)
     prof = {"mg_gs_level0": (10, 2.0), "cg_dir_spmv": (5, 1.0), "mg_restrict": (50, 3.0)}
     r = bench.step_roofline(prof, 1000, 3, 4, ms_total=4.0, ms_host=8.0, peak=100.0)
-    want_bytes = 16 * 1000 * 10 + 28 * 1000 * 5
+    want_bytes = 16 * 1000 * 10 + 20 * 1000 * 5
+    assert bench.algo_bytes_per_cell("cg_dir_spmv", 2, 4) == 24
+    assert bench.algo_bytes_per_cell("cg_dir_spmv", 3, 8) == 56
     assert r["bytes"] == want_bytes
     assert r["achieved"] == pytest.approx(want_bytes / 4e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 100.0)

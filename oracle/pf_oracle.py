@@ -38,12 +38,12 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 from scipy.special import eval_legendre
 
-MODEL_CDI, MODEL_SB, MODEL_ISODI = 0, 1, 2
+MODEL_CDI, MODEL_SB, MODEL_ISODI, MODEL_ACDI = 0, 1, 2, 3
 FORCE_EB, FORCE_CSF, FORCE_LCSF = 0, 1, 2
 SCHEME_RK4, SCHEME_FE = 0, 1
 MOMENTUM_ADVECTIVE, MOMENTUM_CONSISTENT = 0, 1
 
-_MODELS = {"cdi": 0, "sb": 1, "isodi": 2}
+_MODELS = {"cdi": 0, "sb": 1, "isodi": 2, "acdi": 3}
 _FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 _SCHEMES = {"rk4": 0, "fe": 1}
 _MOMENTUM = {"advective": 0, "consistent": 1}
@@ -216,6 +216,33 @@ def face_beta(phi, g, p):
 
 
 # ----------------------------------------------------------------------------
+# ACDI: the accurate conservative diffuse-interface model (Jain, J. Comput.
+# Phys. 469, 2022), the model the 256^2 and 384^3 workloads name; this paper
+# does not define it. Same flux form as CDI with the sharpening term evaluated
+# through the signed-distance-like variable psi.
+# ----------------------------------------------------------------------------
+ACDI_EPS0 = 1e-20
+
+
+def acdi_psi(phi, eps):
+    """psi = eps ln((phi + eps0) / (1 - phi + eps0)) of clip(phi, 0, 1), eps0 = 1e-20.
+
+    For the equilibrium profile phi = [1 + tanh(s / (2 eps))] / 2 this is the
+    signed distance s (up to eps0); eps0 keeps it finite where phi is 0 or 1
+    (|psi| <= 46.1 eps), and the clip keeps the logarithm real (reading).
+    """
+    p = np.clip(phi, 0.0, 1.0)
+    return eps * np.log((p + ACDI_EPS0) / (1.0 - p + ACDI_EPS0))
+
+
+def acdi_sharpening(psi_f, eps):
+    """The ACDI sharpening coefficient (1/4) [1 - tanh^2(psi_f / (2 eps))]: phi (1 - phi)
+    of the equilibrium profile at the signed distance psi_f."""
+    t = np.tanh(psi_f / (2.0 * eps))
+    return 0.25 * (1.0 - t * t)
+
+
+# ----------------------------------------------------------------------------
 # phase-field right-hand side (Eq. 1 with g from Table 1)
 # ----------------------------------------------------------------------------
 def phase_rhs(phi, u, g, p, gamma):
@@ -227,16 +254,27 @@ def phase_rhs(phi, u, g, p, gamma):
     SB adds gamma [eps lap(phi) - psi'/eps + eps |grad phi| kappa] and ISODI
     gamma [eps lap(phi) - psi'/eps + phi (1 - phi) kappa] to the same
     conservative central advective term.
+    ACDI (Jain 2022; not in this paper) has the CDI flux with the sharpening
+    term (1/4) [1 - tanh^2(psi_f / (2 eps))] n_f, psi = acdi_psi(phi), psi_f
+    the two-cell average and n the cell normals of psi, two-cell averaged.
     """
     eps, dn = p["eps"], p["delta_n"]
     model = p["model"]
     rhs = np.zeros_like(phi)
-    if model == MODEL_CDI:
-        n, _ = normals(phi, g, dn)
+    if model in (MODEL_CDI, MODEL_ACDI):
+        if model == MODEL_ACDI:
+            psi = acdi_psi(phi, eps)
+            n, _ = normals(psi, g, dn)
+        else:
+            n, _ = normals(phi, g, dn)
         for d in range(g.dim):
             pf = face_avg(phi, g, d)
             nf = face_avg(n[d], g, d)
-            F = u[d] * pf - gamma * (eps * face_diff(phi, g, d) - pf * (1.0 - pf) * nf)
+            if model == MODEL_ACDI:
+                sharp = acdi_sharpening(face_avg(psi, g, d), eps)
+            else:
+                sharp = pf * (1.0 - pf)
+            F = u[d] * pf - gamma * (eps * face_diff(phi, g, d) - sharp * nf)
             rhs = rhs - (S(F, g, d, 1) - F) / g.h
         return rhs
     for d in range(g.dim):

@@ -19,7 +19,7 @@ import math
 import numpy as np
 
 # Enumerations shared with the C ABI (same integer values as include/pf.h).
-MODELS = {"cdi": 0, "sb": 1, "isodi": 2}
+MODELS = {"cdi": 0, "sb": 1, "isodi": 2, "acdi": 3}
 FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 SCHEMES = {"rk4": 0, "fe": 1}

@@ -1,7 +1,7 @@
 """Throughput of the fractional step (pf_step) on one GB300, in Mcell-steps/s.
 
 Default workload: the 384^3 mode-2 oscillating drop (density and viscosity
-ratio 10, CDI + energy-based force, mixed precision: float32 stencils and
+ratio 10, ACDI phase field + energy-based force, mixed precision: float32 stencils and
 V-cycles inside a refinement to float64 accuracy). One timed step is one
 pf_step: four RK stages, each with its phase-field/momentum stage kernels and
 one variable-coefficient Poisson solve; by default (--graph 1) each step is
@@ -53,13 +53,13 @@ def workload(name, n=None):
     if name == "osc384":
         p = I.oscillating_drop_384(precision="mixed", n=n or 384)
         desc = (f"3D mode-2 oscillating drop {p['n'][0]}^3 periodic, R=0.25, a=0.05R, "
-                "rho ratio 10, mu ratio 10, CDI + EB, mixed precision")
+                "rho ratio 10, mu ratio 10, ACDI + EB, mixed precision")
     elif name == "osc384_fp64":
         p = I.oscillating_drop_384(precision="fp64", n=n or 384)
         desc = f"same drop {p['n'][0]}^3, plain FP64"
     elif name == "drop256":
         p = I.static_drop_256_r1000(precision="mixed")
-        desc = "2D static drop 256^2, rho ratio 1000, mu ratio 100, CDI + EB, mixed"
+        desc = "2D static drop 256^2, rho ratio 1000, mu ratio 100, ACDI + EB, mixed"
     elif name in ("batch256", "batch256_fp64"):
         prec = "fp64" if name.endswith("fp64") else "mixed"
         plist = I.batch_manifest(count=256, precision=prec,
@@ -70,11 +70,12 @@ def workload(name, n=None):
                 f"static or mode-2, {prec}, {cells} cells in total")
         return plist, desc
     elif name == "osc384_consistent":
-        p = dict(I.oscillating_drop_384(precision="mixed", n=n or 384), momentum="consistent")
+        p = I.oscillating_drop_384(precision="mixed", n=n or 384, model="cdi")
+        p["momentum"] = "consistent"
         desc = (f"3D mode-2 oscillating drop {p['n'][0]}^3, rho ratio 10, CDI + EB, mixed, "
                 "consistent (conservative) momentum transport")
     elif name == "drop256_consistent":
-        p = dict(I.static_drop_256_r1000(precision="mixed"), momentum="consistent")
+        p = dict(I.static_drop_256_r1000(precision="mixed", model="cdi"), momentum="consistent")
         desc = ("2D static drop 256^2, rho ratio 1000, mu ratio 100, CDI + EB, mixed, "
                 "consistent (conservative) momentum transport")
     elif name == "drop64":
@@ -206,7 +207,7 @@ def job_time(seconds, dist=None, device=None):
     return float(t.item())
 
 
-def algo_bytes_per_cell(cls, dim, w):
+def algo_bytes_per_cell(cls, dim, w, fused_stage=False):
     d = dim
     # the 3D float32 path forms the CG operator's and the finest restriction's
     # coefficients from the cell densities (one array) instead of d face arrays
@@ -228,7 +229,10 @@ def algo_bytes_per_cell(cls, dim, w):
         "ir_residual_f64": 16 + d * w + w,
         # stage kernel: read phi_s, u_s, phi^n, u^n, normals, mu, accumulators;
         # write phi, u*, accumulators (stages 1-2; the first and last move less)
-        "stage": (1 + d + 1 + d + d + 1 + 1 + d) * w + (1 + d + 1 + d) * w,
+        # fused stage (no cell pass): read phi_s, u_s, phi^n, u^n, accumulators;
+        # write phi, u*, accumulators (stages 1-2)
+        "stage": ((1 + d + 1 + d + 1 + d) * w + (1 + d + 1 + d) * w if fused_stage
+                  else (1 + d + 1 + d + d + 1 + 1 + d) * w + (1 + d + 1 + d) * w),
         "cell_pass": w + (d + 1) * w,
         "correct": d * w + 8 + d * w + d * w,
         "divergence": d * w + 8,
@@ -258,7 +262,7 @@ def step_roofline(prof, ncell, dim, w, ms_total, ms_host, peak):
     tot_b, tot_ms = 0.0, 0.0
     for cls in FINEST_CLASSES:
         if cls in prof and prof[cls][0] > 0:
-            bpc = algo_bytes_per_cell(cls, dim, w)
+            bpc = algo_bytes_per_cell(cls, dim, w, fused_stage="cell_pass" not in prof)
             tot_b += bpc * ncell * prof[cls][0]
             tot_ms += prof[cls][1]
     if tot_b == 0.0 or ms_total <= 0:
@@ -563,7 +567,7 @@ def run_ours(args, rank, world, local_rank):
     ranked = sorted(((v[1], k, v[0]) for k, v in prof.items() if v[0] > 0), reverse=True)
     dom_ms, dom, dom_n = ranked[0] if ranked else (0.0, None, 0)
     peak, peak_kind = measured_hbm()
-    bpc = algo_bytes_per_cell(dom, p["dim"], w)
+    bpc = algo_bytes_per_cell(dom, p["dim"], w, fused_stage="cell_pass" not in prof)
     roof = None
     if bpc is not None and dom_n > 0:
         avg_s = dom_ms / dom_n / 1e3

@@ -58,7 +58,11 @@ typedef enum {
     PF_ERR_WORKSPACE = 7       /* workspace pointer misaligned or too small */
 } pf_status;
 
-enum { PF_CDI = 0, PF_SB = 1, PF_ISODI = 2 };               /* phase-field model (Table 1) */
+enum { PF_CDI = 0, PF_SB = 1, PF_ISODI = 2,                /* phase-field model (Table 1) */
+       PF_ACDI = 3 };  /* accurate conservative diffuse interface (Jain, J. Comput. Phys. 469,
+                          2022; not in the paper): the CDI flux with the sharpening term
+                          (1/4)[1 - tanh^2(psi_f / (2 eps))] n_f, psi = eps ln((phi + e0) /
+                          (1 - phi + e0)) of clip(phi, 0, 1), e0 = 1e-20, n the normals of psi */
 enum { PF_FORCE_EB = 0, PF_FORCE_CSF = 1, PF_FORCE_LCSF = 2 }; /* surface tension force */
 enum { PF_FP64 = 0, PF_MIXED = 1 };                         /* precision of stencils and V-cycles */
 enum { PF_RK4_PROJ = 0, PF_FE = 1 };                        /* time integrator */
@@ -70,7 +74,7 @@ typedef struct {
     int dim;              /* 2 or 3 */
     int n[3];             /* cells per axis (n[2] = 1 in 2D); each >= 4; the box is n[d]*L/n[0] long */
     double L;             /* box length along x; dx = L / n[0] (uniform spacing) */
-    int model;            /* PF_CDI, PF_SB or PF_ISODI */
+    int model;            /* PF_CDI, PF_SB, PF_ISODI or PF_ACDI */
     int force;            /* PF_FORCE_EB, PF_FORCE_CSF or PF_FORCE_LCSF */
     int precision;        /* PF_FP64: everything in float64.
                              PF_MIXED: phi, u and the stencils in float32, the double-well
@@ -125,7 +129,13 @@ typedef struct {
                              (tensor and bulk copies completing on mbarriers) where the grid
                              allows (n[0] % 4 == 0, n[0] >= 40); 1: by per-thread cp.async
                              chunks. Same arithmetic, same results. */
-    int reserved[2];      /* must be zero */
+    int stage_kernel;     /* 3D mixed path, CDI or ACDI with the EB force and advective transport:
+                             0 (default) one fused kernel per stage forms the normals, mu and
+                             psi in shared memory and evaluates the right-hand sides (no HBM
+                             round trip of the derived fields; n[0] % 4 == 0, n[0] >= 40,
+                             n[1] >= 12); 1: a cell-pass kernel writes them to the workspace
+                             and the stage kernel reads them back. Same arithmetic. */
+    int reserved[1];      /* must be zero */
 } pf_params;
 
 typedef struct {

@@ -19,7 +19,7 @@ from .binding import (PFError, pf_batch_context, pf_batch_destroy, pf_batch_init
                       pf_set_field, pf_set_state, pf_state_bytes, pf_step, pf_sync,
                       pf_workspace_size)
 
-MODELS = {"cdi": 0, "sb": 1, "isodi": 2}
+MODELS = {"cdi": 0, "sb": 1, "isodi": 2, "acdi": 3}
 FORCES = {"eb": 0, "csf": 1, "lcsf": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 SCHEMES = {"rk4": 0, "fe": 1}
@@ -52,7 +52,7 @@ def make_params(p: dict) -> B.pf_params:
               "dt", "delta_n", "poisson_rtol", "R", "pert_amp", "bound_tol", "inner_tol"):
         setattr(q, k, float(p.get(k, 0.0) or 0.0))
     for k in ("poisson_maxit", "pert_mode", "mg_pre", "mg_post", "use_graph", "wall_y",
-              "mg_coarse_cells", "sweep_staging"):
+              "mg_coarse_cells", "sweep_staging", "stage_kernel"):
         setattr(q, k, int(p.get(k, 0) or 0))
     return q
 

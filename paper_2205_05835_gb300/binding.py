@@ -53,7 +53,8 @@ class pf_params(ctypes.Structure):
         ("shape", ctypes.c_int),
         ("mg_coarse_cells", ctypes.c_int),
         ("sweep_staging", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("stage_kernel", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 

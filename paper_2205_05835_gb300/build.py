@@ -17,8 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpf.so")
-SOURCES = ["pf_stage.cu", "pf_stage3d.cu", "pf_poisson.cu", "pf_mg3d.cu", "pf_sweep_tma.cu",
-           "pf_capi.cu", "pf_batch.cu", "pf_adjoint.cu"]
+SOURCES = ["pf_stage.cu", "pf_stage3d.cu", "pf_stage_fused.cu", "pf_poisson.cu", "pf_mg3d.cu",
+           "pf_sweep_tma.cu", "pf_capi.cu", "pf_batch.cu", "pf_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

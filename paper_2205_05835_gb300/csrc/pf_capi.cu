@@ -151,7 +151,7 @@ pf_status validate(const pf_params* p, std::string& why) {
     }
     if (p->dim == 2 && p->n[2] != 1) { why = "n[2] must be 1 in 2D"; return PF_ERR_INVALID; }
     if (nc > (1LL << 30)) { why = "grid too large (more than 2^30 cells)"; return PF_ERR_INVALID; }
-    if (p->model < 0 || p->model > 2) { why = "bad model"; return PF_ERR_INVALID; }
+    if (p->model < 0 || p->model > 3) { why = "bad model"; return PF_ERR_INVALID; }
     if (p->force < 0 || p->force > 2) { why = "bad force"; return PF_ERR_INVALID; }
     if (p->precision < 0 || p->precision > 1) { why = "bad precision"; return PF_ERR_INVALID; }
     if (p->scheme < 0 || p->scheme > 1) { why = "bad scheme"; return PF_ERR_INVALID; }
@@ -205,7 +205,11 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "sweep_staging must be 0 or 1";
         return PF_ERR_INVALID;
     }
-    for (int i = 0; i < 2; ++i)
+    if (p->stage_kernel != 0 && p->stage_kernel != 1) {
+        why = "stage_kernel must be 0 or 1";
+        return PF_ERR_INVALID;
+    }
+    for (int i = 0; i < 1; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
     return PF_OK;
 }
@@ -291,6 +295,9 @@ struct ImplT final : Impl {
         ph.mu_out_f = float(prm.mu_out);
         ph.dmu_f = float(prm.mu_in) - float(prm.mu_out);
         ph.delta_n_f = float(prm.delta_n);
+        ph.fused_stage = 0;
+        if (DIM == 3 && sizeof(T) == sizeof(float) && prm.stage_kernel == 0)
+            ph.fused_stage = stage_fused_ok(g, ph) ? 1 : 0;
         for (int d = 0; d < 3; ++d) uN[d] = uS[d] = uStar[d] = accu[d] = nrm[d] = nullptr;
         // multigrid hierarchy geometry
         H.nlev = 1;
@@ -780,6 +787,7 @@ struct ImplT final : Impl {
     pf_status capture_step() {
         sweep3d_prepare();
         sweep_tma_prepare();
+        stage_fused_prepare();
         coarse_prepare();
         // the legacy default stream cannot be captured: record on a private
         // stream (recording runs nothing); the graph replays on the context's
@@ -842,9 +850,11 @@ struct ImplT final : Impl {
             io.phi_s = phiN;
             for (int d = 0; d < 3; ++d) io.u_s[d] = uN[d];
             io.phi_out = phiA;
-            prof.begin(KC_CELL);
-            launch_cell_pass<T, DIM>(g, ph, phiN, nrm[0], nrm[1], nrm[2], aux, st);
-            prof.end();
+            if (!ph.fused_stage) {
+                prof.begin(KC_CELL);
+                launch_cell_pass<T, DIM>(g, ph, phiN, nrm[0], nrm[1], nrm[2], aux, st);
+                prof.end();
+            }
             prof.begin(KC_STAGE);
             launch_stage<T, DIM>(g, ph, io, 0, 1, dt, dt, 0, st);
             prof.end();
@@ -869,9 +879,11 @@ struct ImplT final : Impl {
             io.phi_s = phin_s[s];
             for (int d = 0; d < 3; ++d) io.u_s[d] = s == 0 ? uN[d] : uS[d];
             io.phi_out = phout[s];
-            prof.begin(KC_CELL);
-            launch_cell_pass<T, DIM>(g, ph, phin_s[s], nrm[0], nrm[1], nrm[2], aux, st);
-            prof.end();
+            if (!ph.fused_stage) {
+                prof.begin(KC_CELL);
+                launch_cell_pass<T, DIM>(g, ph, phin_s[s], nrm[0], nrm[1], nrm[2], aux, st);
+                prof.end();
+            }
             const double wdt = kRK4W[s] * dt;
             const double cdt = s < 3 ? kRK4C[s + 1] * dt : dt;
             prof.begin(KC_STAGE);

@@ -173,6 +173,33 @@ __device__ __forceinline__ float dwell32(float phi, float ch, float cl) {
     return __fadd_rn(q.hi, q.lo);
 }
 
+// ACDI phase field (the accurate conservative diffuse-interface model of Jain,
+// J. Comput. Phys. 469, 2022): psi = eps ln((phi + e0) / (1 - phi + e0)) of
+// clip(phi, 0, 1) with e0 = 1e-20 (finite where phi is 0 or 1), and the
+// sharpening coefficient (1/4) [1 - tanh^2(psi_f / (2 eps))] of a face value
+// psi_f. Float64: the library's log and tanh. Float32 (mixed path): the fast
+// logarithm of the ratio, and the coefficient in the equivalent form
+// e / (1 + e)^2 with e = exp(-|psi_f| / eps) (1 - tanh^2(y) = 4 e^{-2|y|} /
+// (1 + e^{-2|y|})^2), through the fast exponential: a few ulp of float32.
+constexpr double kAcdiE0 = 1e-20;
+__device__ __forceinline__ double acdi_psi(double p, double eps) {
+    p = p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
+    return eps * log((p + kAcdiE0) / (1.0 - p + kAcdiE0));
+}
+__device__ __forceinline__ float acdi_psi(float p, float eps) {
+    p = p < 0.f ? 0.f : (p > 1.f ? 1.f : p);
+    return eps * __logf(__fdividef(p + float(kAcdiE0), 1.f - p + float(kAcdiE0)));
+}
+__device__ __forceinline__ double acdi_sharp(double psif, double eps) {
+    const double t = tanh(psif / (2.0 * eps));
+    return 0.25 * (1.0 - t * t);
+}
+__device__ __forceinline__ float acdi_sharp(float psif, float eps) {
+    const float e = __expf(-fabsf(psif) * __frcp_rn(eps));
+    const float q = 1.f + e;
+    return __fdividef(e, q * q);
+}
+
 // a / b: IEEE division in float64, multiplication by the correctly rounded
 // reciprocal in float32.
 __device__ __forceinline__ double divq(double a, double b) { return a / b; }

@@ -53,6 +53,7 @@ __host__ __device__ inline double ih2_of(const Dims& g, double) { return g.ih2; 
 struct Phys {
     int dim, model, force;
     int momentum;                         // 0 advective, 1 consistent (conservative) transport
+    int fused_stage;                      // 1: 3D float32 stage with the cell pass fused in
     double sigma, eps, rho_in, rho_out, mu_in, mu_out, delta_n;
     double drho, dmu;                     // rho_in - rho_out, mu_in - mu_out
     float sigma_f, eps_f, rho_out_f, drho_f, mu_out_f, dmu_f, delta_n_f;
@@ -199,9 +200,16 @@ bool restrict3d_ok(const Dims& fine);
 // densities instead of the level's face arrays.
 void launch_restrict3d(const MGLevel<float>& F, const MGLevel<float>& C, const float* rho,
                        const CGScalars* sc, cudaStream_t s);
+// The fused stage of the 3D float32 path (pf_stage_fused.cu): cell pass and
+// stage in one kernel for CDI / ACDI with the EB force and advective transport.
+bool stage_fused_ok(const Dims& g, const Phys& ph);
+void stage_fused_prepare();
+void launch_stage_fused(const Dims& g, const Phys& ph, const StageIO<float>& io, int stage,
+                        int scheme, double wdt, double cdt, int write_rhs, cudaStream_t s);
 // Column-marching per-stage kernels for 3D float32 grids (pf_stage3d.cu).
+// psi != nullptr (ACDI): normals of psi = acdi_psi(phi), and psi written
 void launch_cell_pass_mu3d(const Dims& g, const Phys& ph, const float* phi, float* n0, float* n1,
-                           float* n2, float* mu, cudaStream_t s);
+                           float* n2, float* mu, float* psi, cudaStream_t s);
 bool divergence3d_ok(const Dims& g);
 void launch_divergence3d(const Dims& g, const float* const* u, double inv_tau, double* b,
                          RedBuf rb, CGScalars* sc, cudaStream_t s);

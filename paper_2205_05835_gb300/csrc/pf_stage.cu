@@ -130,10 +130,27 @@ __device__ __forceinline__ void normal_at(const T* __restrict__ phi, const Nbr<D
     for (int d = 0; d < DIM; ++d) n[d] = divq(gr[d], den);
 }
 
+// ACDI: the normal of psi (central gradient of psi of the neighbours' phi)
+template <typename T, int DIM>
+__device__ __forceinline__ void normal_psi(const T* __restrict__ phi, const Nbr<DIM>& nb, T eps,
+                                           T inv2h, T dn, T (&n)[3]) {
+    auto ps = [&](int oi, int oj, int ok) { return acdi_psi(ldg(phi, nb.at(oi, oj, ok)), eps); };
+    T gr[3];
+    gr[0] = (ps(1, 0, 0) - ps(-1, 0, 0)) * inv2h;
+    gr[1] = (ps(0, 1, 0) - ps(0, -1, 0)) * inv2h;
+    gr[2] = DIM == 3 ? (ps(0, 0, 1) - ps(0, 0, -1)) * inv2h : T(0);
+    T s = gr[0] * gr[0] + gr[1] * gr[1];
+    if (DIM == 3) s += gr[2] * gr[2];
+    const T den = sqrt(s) + dn;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) n[d] = divq(gr[d], den);
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* __restrict__ n1,
-            T* __restrict__ n2, T* __restrict__ mu_out, T* __restrict__ kap_out) {
+            T* __restrict__ n2, T* __restrict__ mu_out, T* __restrict__ kap_out,
+            T* __restrict__ psi_out) {
     const PC<T> pcn = pc_of(ph, T());
     const double sh = 6.0 * ph.sigma;
     const double c_dw = sh / ph.eps;         // (6 sigma / eps), float64 double-well factor
@@ -145,11 +162,17 @@ k_cell_pass(Dims g, Phys ph, const T* __restrict__ phi, T* __restrict__ n0, T* _
     const T inv_h = ih_of(g, T()), inv2h = i2h_of(g, T()), inv_h2 = ih2_of(g, T());
     const T dn = pcn.delta_n;
     T n[3], mag;
-    normal_at<T, DIM>(phi, nb, 0, 0, 0, inv2h, dn, n, mag);
+    const T pc = ldg(phi, idx);
+    if (psi_out) {
+        // ACDI: normals of psi, and psi itself for the face sharpening terms
+        normal_psi<T, DIM>(phi, nb, pcn.eps, inv2h, dn, n);
+        psi_out[idx] = acdi_psi(pc, pcn.eps);
+    } else {
+        normal_at<T, DIM>(phi, nb, 0, 0, 0, inv2h, dn, n, mag);
+    }
     n0[idx] = n[0];
     n1[idx] = n[1];
     if (DIM == 3) n2[idx] = n[2];
-    const T pc = ldg(phi, idx);
     if (mu_out) {
         T lap = T(0);
 #pragma unroll
@@ -186,23 +209,25 @@ template <typename T, int DIM>
 void launch_cell_pass(const Dims& g, const Phys& ph, const T* phi, T* nrm0, T* nrm1, T* nrm2,
                       T* aux, cudaStream_t s) {
     // aux holds mu for the EB force, kappa otherwise; kappa for SB/ISODI with the
-    // EB force is stored after the mu array (aux + ncell).
+    // EB force, or psi for ACDI, is stored after it (aux + ncell).
     T* mu = nullptr;
     T* kap = nullptr;
+    T* psi = ph.model == 3 ? aux + g.ncell : nullptr;
     if (ph.force == 0) {
         mu = aux;
-        if (ph.model != 0) kap = aux + g.ncell;
+        if (ph.model == 1 || ph.model == 2) kap = aux + g.ncell;
     } else {
         kap = aux;
     }
     if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        if (ph.fused_stage) return;   // the fused stage kernel forms them itself
         if (mu != nullptr && kap == nullptr) {
-            launch_cell_pass_mu3d(g, ph, phi, nrm0, nrm1, nrm2, mu, s);
+            launch_cell_pass_mu3d(g, ph, phi, nrm0, nrm1, nrm2, mu, psi, s);
             return;
         }
     }
     k_cell_pass<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(g, ph, phi, nrm0, nrm1,
-                                                                              nrm2, mu, kap);
+                                                                              nrm2, mu, kap, psi);
 }
 
 // ---------------------------------------------------------------------------
@@ -225,7 +250,11 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
 
     // ---------------- phase field (Eq. 1, Table 1) ----------------
     T kphi = T(0);
-    if (ph.model == 0) {
+    if (ph.model == 0 || ph.model == 3) {
+        // CDI flux; ACDI: the sharpening coefficient from psi at the face
+        const bool acdi = ph.model == 3;
+        const T* __restrict__ psi = io.aux + g.ncell;
+        const T psc = acdi ? ldg(psi, idx) : T(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const T* __restrict__ nd = io.nrm[d];
@@ -234,14 +263,18 @@ k_stage(Dims g, Phys ph, StageIO<T> io, int stage, int scheme, T wdt, T cdt, int
             T pm = ldg(phi, nb.ax(d, -1));
             T pf = T(0.5) * (pc + pm);
             T nf = T(0.5) * (ldg(nd, idx) + ldg(nd, nb.ax(d, -1)));
-            T Flo = ldg(ud, idx) * pf - gam * (eps * ((pc - pm) * inv_h) - pf * (T(1) - pf) * nf);
+            const T shlo = acdi ? acdi_sharp(T(0.5) * (psc + ldg(psi, nb.ax(d, -1))), eps)
+                                : pf * (T(1) - pf);
+            T Flo = ldg(ud, idx) * pf - gam * (eps * ((pc - pm) * inv_h) - shlo * nf);
             // high face (between c and c + e_d)
             int ip = nb.ax(d, 1);
             T pp = ldg(phi, ip);
             T pf2 = T(0.5) * (pp + pc);
             T nf2 = T(0.5) * (ldg(nd, ip) + ldg(nd, idx));
+            const T shhi = acdi ? acdi_sharp(T(0.5) * (ldg(psi, ip) + psc), eps)
+                                : pf2 * (T(1) - pf2);
             T Fhi = ldg(ud, nb.axc(d, d, 1)) * pf2 -
-                    gam * (eps * ((pp - pc) * inv_h) - pf2 * (T(1) - pf2) * nf2);
+                    gam * (eps * ((pp - pc) * inv_h) - shhi * nf2);
             // no flux through a wall
             if (wall_face(g, c.j, 2 * d)) Flo = T(0);
             if (wall_face(g, c.j, 2 * d + 1)) Fhi = T(0);
@@ -471,7 +504,11 @@ k_stage3d(Dims g, Phys ph, StageIO<float> io, int stage, int scheme, float wdt, 
 
         // ---------------- phase field (Eq. 1, Table 1) ----------------
         float kphi = 0.f;
-        if (ph.model == 0) {
+        if (ph.model == 0 || ph.model == 3) {
+            // CDI flux; ACDI: the sharpening coefficient from psi at the face
+            const bool acdi = ph.model == 3;
+            const float* __restrict__ psi = io.aux + g.ncell;
+            const float psc = acdi ? at(psi, 0) : 0.f;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const float* __restrict__ nd = io.nrm[d];
@@ -479,11 +516,15 @@ k_stage3d(Dims g, Phys ph, StageIO<float> io, int stage, int scheme, float wdt, 
                 const float pm = at(phi, om[d]);
                 const float pf = 0.5f * (pc + pm);
                 const float nf = 0.5f * (at(nd, 0) + at(nd, om[d]));
-                const float Flo = at(ud, 0) * pf - gam * (eps * ((pc - pm) * inv_h) - pf * (1.f - pf) * nf);
+                const float shlo =
+                    acdi ? acdi_sharp(0.5f * (psc + at(psi, om[d])), eps) : pf * (1.f - pf);
+                const float Flo = at(ud, 0) * pf - gam * (eps * ((pc - pm) * inv_h) - shlo * nf);
                 const float pp = at(phi, op[d]);
                 const float pf2 = 0.5f * (pp + pc);
                 const float nf2 = 0.5f * (at(nd, op[d]) + at(nd, 0));
-                const float Fhi = at(ud, op[d]) * pf2 - gam * (eps * ((pp - pc) * inv_h) - pf2 * (1.f - pf2) * nf2);
+                const float shhi =
+                    acdi ? acdi_sharp(0.5f * (at(psi, op[d]) + psc), eps) : pf2 * (1.f - pf2);
+                const float Fhi = at(ud, op[d]) * pf2 - gam * (eps * ((pp - pc) * inv_h) - shhi * nf2);
                 kphi = kphi - (Fhi - Flo) * inv_h;
             }
         } else {
@@ -608,6 +649,10 @@ template <typename T, int DIM>
 void launch_stage(const Dims& g, const Phys& ph, const StageIO<T>& io, int stage, int scheme,
                   double wdt, double cdt, int write_rhs, cudaStream_t s) {
     if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+        if (ph.fused_stage) {
+            launch_stage_fused(g, ph, io, stage, scheme, wdt, cdt, write_rhs, s);
+            return;
+        }
         if (ph.momentum == 1) {
             k_stage<T, DIM><<<row_grid(g, kThreads, 1 << 30), kThreads, 0, s>>>(
                 g, ph, io, stage, scheme, T(wdt), T(cdt), write_rhs);

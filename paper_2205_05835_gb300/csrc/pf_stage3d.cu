@@ -6,7 +6,8 @@
 // pf_stage.cu, cell by cell.
 //   * cell pass for the energy-based force with the CDI model: normals
 //     n = grad_c phi / (|grad_c phi| + delta_n) and the chemical potential
-//     mu = (6 sigma / eps) psi'(phi) - 6 sigma eps lap(phi) (Eq. ac_mu);
+//     mu = (6 sigma / eps) psi'(phi) - 6 sigma eps lap(phi) (Eq. ac_mu); with
+//     the ACDI model the normals are those of psi (acdi_psi), also written;
 //   * divergence b = D u* / tau of the face velocities and its mean;
 //   * correction u = u* - tau beta G p with the float32 face coefficients.
 #include "pf_device.cuh"
@@ -44,7 +45,8 @@ struct CellPassArgs {
     float* n1;
     float* n2;
     float* mu;
-    float dn, c_dw_hi, c_dw_lo, c_lap;
+    float* psi;        // ACDI: psi of phi (written), normals of psi; nullptr: normals of phi
+    float dn, c_dw_hi, c_dw_lo, c_lap, eps;
     int zc;
 };
 
@@ -60,16 +62,31 @@ __global__ void __launch_bounds__(ZT) k_cell_pass_mu3d(CellPassArgs A) {
     float* __restrict__ n1 = A.n1;
     float* __restrict__ n2 = A.n2;
     float* __restrict__ mu = A.mu;
+    float* __restrict__ psi = A.psi;
+    const float eps = A.eps;
     float pm = __ldg(phi + (z0 == 0 ? g.nz - 1 : z0 - 1) * sz + c.col);
     float pc = __ldg(phi + z0 * sz + c.col);
+    // ACDI: psi of the column's planes k - 1, k
+    float sm = psi ? acdi_psi(pm, eps) : 0.f, sc_ = psi ? acdi_psi(pc, eps) : 0.f;
 #pragma unroll 2
     for (int k = z0; k < z1; ++k) {
         const int idx = k * sz + c.col;
         const float pp = __ldg(phi + (k + 1 == g.nz ? 0 : k + 1) * sz + c.col);
         const float xm = __ldg(phi + idx + c.ox_m), xp = __ldg(phi + idx + c.ox_p);
         const float ym = __ldg(phi + idx + c.oy_m), yp = __ldg(phi + idx + c.oy_p);
-        // normal (central gradient)
-        const float g0 = (xp - xm) * inv2h, g1 = (yp - ym) * inv2h, g2 = (pp - pm) * inv2h;
+        // normal (central gradient of phi, or of psi for ACDI)
+        float g0, g1, g2, sp = 0.f;
+        if (psi) {
+            sp = acdi_psi(pp, eps);
+            g0 = (acdi_psi(xp, eps) - acdi_psi(xm, eps)) * inv2h;
+            g1 = (acdi_psi(yp, eps) - acdi_psi(ym, eps)) * inv2h;
+            g2 = (sp - sm) * inv2h;
+            psi[idx] = sc_;
+        } else {
+            g0 = (xp - xm) * inv2h;
+            g1 = (yp - ym) * inv2h;
+            g2 = (pp - pm) * inv2h;
+        }
         float s = g0 * g0 + g1 * g1;
         s += g2 * g2;
         const float den = sqrtf(s) + A.dn;
@@ -84,6 +101,8 @@ __global__ void __launch_bounds__(ZT) k_cell_pass_mu3d(CellPassArgs A) {
         mu[idx] = dwell32(pc, A.c_dw_hi, A.c_dw_lo) - A.c_lap * lap;
         pm = pc;
         pc = pp;
+        sm = sc_;
+        sc_ = sp;
     }
 }
 
@@ -201,7 +220,7 @@ dim3 zgrid(const Dims& g, int zc) {
 }  // namespace
 
 void launch_cell_pass_mu3d(const Dims& g, const Phys& ph, const float* phi, float* n0, float* n1,
-                           float* n2, float* mu, cudaStream_t s) {
+                           float* n2, float* mu, float* psi, cudaStream_t s) {
     CellPassArgs a;
     a.g = g;
     a.phi = phi;
@@ -209,6 +228,8 @@ void launch_cell_pass_mu3d(const Dims& g, const Phys& ph, const float* phi, floa
     a.n1 = n1;
     a.n2 = n2;
     a.mu = mu;
+    a.psi = psi;
+    a.eps = ph.eps_f;
     const double sh = 6.0 * ph.sigma;
     const double c_dw = sh / ph.eps;
     a.dn = float(ph.delta_n);

@@ -88,18 +88,19 @@ def static_drop_64():
                           mu_in=0.1, mu_out=0.1, steps=200))
 
 
-def static_drop_256_r1000(force="eb", precision="fp64"):
-    """256^2 static drop, density ratio 1000, viscosity ratio 100, CDI."""
+def static_drop_256_r1000(force="eb", precision="fp64", model="acdi"):
+    """256^2 static drop, density ratio 1000, viscosity ratio 100, ACDI phase field."""
     return finalize(_base(dim=2, n=(256, 256, 1), rho_in=240.0, rho_out=0.24,
                           mu_in=0.1, mu_out=0.001, force=force, precision=precision,
-                          steps=2000))
+                          model=model, steps=2000))
 
 
-def oscillating_drop_384(precision="mixed", n=384, steps=500):
-    """384^3 mode-2 oscillating drop, amplitude 0.05 R, density/viscosity ratio 10."""
+def oscillating_drop_384(precision="mixed", n=384, steps=500, model="acdi"):
+    """384^3 mode-2 oscillating drop, amplitude 0.05 R, density/viscosity ratio 10,
+    ACDI phase field, energy-based force."""
     return finalize(_base(dim=3, n=(n, n, n), rho_in=10.0, rho_out=1.0,
                           mu_in=0.01, mu_out=0.001, pert_mode=2, pert_amp=0.05,
-                          precision=precision, poisson_rtol=1e-10, steps=steps))
+                          precision=precision, model=model, poisson_rtol=1e-10, steps=steps))
 
 
 def oscillating_drop_2d_256():

@@ -65,11 +65,15 @@ def test_workspace_size_and_validation(pf):
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
     bad = pf.make_params(I.static_drop_64())
-    bad.reserved[1] = 1
+    bad.reserved[0] = 1
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
     bad = pf.make_params(I.static_drop_64())
     bad.sweep_staging = 2
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(bad)
+    bad = pf.make_params(I.static_drop_64())
+    bad.stage_kernel = 2
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
 
@@ -172,7 +176,8 @@ def test_momentum_transport_validation(pf):
 
     ok = pf.make_params(I.small_case(dim=2, n=32, momentum="consistent"))
     assert pf.pf_workspace_size(ok) > 0
-    for bad in (dict(momentum="consistent", model="sb"), dict(momentum="consistent", model="isodi")):
+    for bad in (dict(momentum="consistent", model="sb"), dict(momentum="consistent", model="isodi"),
+                dict(momentum="consistent", model="acdi")):
         q = pf.make_params(I.small_case(dim=2, n=32, **bad))
         with pytest.raises(pf.PFError) as e:
             pf.pf_workspace_size(q)

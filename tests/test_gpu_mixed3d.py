@@ -42,10 +42,11 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
 
 
-@pytest.mark.parametrize("n", [(40, 24, 16), (32, 16, 16)])
-def test_mixed_3d_steps_match_oracle(pf, n):
+@pytest.mark.parametrize("n,model", [((40, 24, 16), "cdi"), ((32, 16, 16), "cdi"),
+                                     ((40, 24, 16), "acdi")])
+def test_mixed_3d_steps_match_oracle(pf, n, model):
     steps = 3
-    p = I.small_case(dim=3, n=n[0], precision="mixed", poisson_rtol=1e-10)
+    p = I.small_case(dim=3, n=n[0], precision="mixed", poisson_rtol=1e-10, model=model)
     p["n"] = n
     p = I.finalize(p)
     po = O.params_from(p)
@@ -58,7 +59,7 @@ def test_mixed_3d_steps_match_oracle(pf, n):
     errs = {"phi": rel(sim.field("phi"), st.phi), "p": rel(sim.field("p"), st.p)}
     for c, ref in zip("uvw", st.u):
         errs[c] = rel(sim.field(c), ref)
-    print("mixed 3D", n, errs)
+    print("mixed 3D", model, n, errs)
     sim.close()
     assert errs["phi"] < 1e-5, errs
     assert max(errs["u"], errs["v"], errs["w"]) < 2e-3, errs

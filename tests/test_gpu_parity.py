@@ -55,7 +55,7 @@ def test_init_profile(pf, dim, n, mode):
 # --------------------------------------------------------------------------
 # operator parity: phase-field and momentum right-hand sides
 # --------------------------------------------------------------------------
-CASES = [(m, f) for m in ("cdi", "sb", "isodi") for f in ("eb", "csf", "lcsf")]
+CASES = [(m, f) for m in ("cdi", "sb", "isodi", "acdi") for f in ("eb", "csf", "lcsf")]
 
 
 @pytest.mark.parametrize("model,force", CASES)
@@ -80,7 +80,8 @@ def test_rhs_parity_fp64(pf, model, force, dim, n):
     sim.close()
 
 
-@pytest.mark.parametrize("model,force", [("cdi", "eb"), ("isodi", "lcsf"), ("sb", "csf")])
+@pytest.mark.parametrize("model,force", [("cdi", "eb"), ("isodi", "lcsf"), ("sb", "csf"),
+                                         ("acdi", "eb"), ("acdi", "csf")])
 def test_rhs_parity_mixed(pf, model, force):
     """float32 stencils: relative to the field scale, within 2e-5 (phase field) and
     1e-4 (momentum, where the force is a difference of O(1/eps) terms)."""
@@ -196,7 +197,8 @@ def run_both(pf, p, steps):
 
 @pytest.mark.parametrize("model,force,scheme", [
     ("cdi", "eb", "rk4"), ("cdi", "csf", "rk4"), ("cdi", "lcsf", "rk4"),
-    ("sb", "eb", "rk4"), ("isodi", "eb", "fe"), ("sb", "lcsf", "fe")])
+    ("sb", "eb", "rk4"), ("isodi", "eb", "fe"), ("sb", "lcsf", "fe"),
+    ("acdi", "eb", "rk4"), ("acdi", "lcsf", "fe")])
 def test_step_parity_fp64_2d(pf, model, force, scheme):
     p = I.small_case(dim=2, n=40, model=model, force=force, scheme=scheme,
                      poisson_rtol=1e-13, poisson_maxit=300, gamma_min=0.05)
@@ -212,9 +214,9 @@ def test_step_parity_fp64_2d(pf, model, force, scheme):
     sim.close()
 
 
-@pytest.mark.parametrize("force", ["eb", "lcsf"])
-def test_step_parity_fp64_3d(pf, force):
-    p = I.small_case(dim=3, n=16, force=force, poisson_rtol=1e-13, poisson_maxit=300)
+@pytest.mark.parametrize("model,force", [("cdi", "eb"), ("cdi", "lcsf"), ("acdi", "eb")])
+def test_step_parity_fp64_3d(pf, model, force):
+    p = I.small_case(dim=3, n=16, model=model, force=force, poisson_rtol=1e-13, poisson_maxit=300)
     p["n"] = (16, 16, 16)
     sim, st = run_both(pf, p, 3)
     for name, ref in (("phi", st.phi), ("u", st.u[0]), ("v", st.u[1]), ("w", st.u[2]),
@@ -411,3 +413,45 @@ def test_tma_staged_sweep_matches_cp_async_sweep(pf, n):
     assert out[0][1] == out[1][1]
     for c in out[0][2]:
         np.testing.assert_array_equal(out[0][2][c], out[1][2][c])
+
+
+@pytest.mark.parametrize("model", ["cdi", "acdi"])
+@pytest.mark.parametrize("n", [(48, 16, 12), (96, 24, 20)])
+def test_fused_stage_rhs_matches_oracle_and_two_kernel_path(pf, model, n):
+    """The fused stage kernel (normals, mu and psi in shared memory) against the
+    FP64 oracle on float32-rounded inputs (2e-5 of the phase-field scale, 1e-4 of
+    the momentum scale), and against the cell-pass + stage kernels it replaces
+    (the same arithmetic: 1e-6 of each field's scale); then two whole RK4 steps
+    of both paths agree to float32 rounding."""
+    p = I.small_case(dim=3, n=n[0], model=model, precision="mixed")
+    p["n"] = n
+    p = I.finalize(p)
+    po = O.params_from(p)
+    g = O.Grid(3, n, p["L"])
+    phi = O.initial_phi(po) + 0.01 * (I.noise(g.shape, 19) - 0.5)
+    u = rand_velocity(g, 23, amp=0.1)
+    out = {}
+    for sk in (0, 1):
+        sim = pf.Simulation(dict(p, stage_kernel=sk), phi0=phi)
+        for d in range(3):
+            sim.set_field("uvw"[d], u[d])
+        out[sk] = sim.eval_rhs(0.2)
+        sim.close()
+    phi32 = phi.astype(np.float32).astype(np.float64)
+    u32 = [c.astype(np.float32).astype(np.float64) for c in u]
+    kphi, ku = out[0]
+    assert rel(kphi, O.phase_rhs(phi32, u32, g, po, 0.2)) < 2e-5
+    want_u = O.momentum_rhs(phi32, u32, g, po)
+    for d in range(3):
+        assert rel(ku[d], want_u[d]) < 1e-4, d
+    assert rel(kphi, out[1][0]) < 1e-6
+    for d in range(3):
+        assert rel(ku[d], out[1][1][d]) < 1e-6, d
+    fields = {}
+    for sk in (0, 1):
+        sim = pf.Simulation(dict(p, stage_kernel=sk, poisson_rtol=1e-10), phi0=phi32)
+        sim.step(2)
+        fields[sk] = {c: sim.field(c) for c in ("phi", "u", "v", "w", "p")}
+        sim.close()
+    for c in fields[0]:
+        assert rel(fields[0][c], fields[1][c]) < 1e-5, c

@@ -59,7 +59,7 @@ def start(p, seed):
 @pytest.mark.parametrize("n,model,force,scheme", [
     ((32, 24), "cdi", "eb", "rk4"), ((32, 24), "cdi", "csf", "rk4"),
     ((40, 36), "cdi", "lcsf", "rk4"), ((32, 24), "sb", "eb", "fe"),
-    ((24, 40), "isodi", "lcsf", "rk4")])
+    ((24, 40), "isodi", "lcsf", "rk4"), ((32, 24), "acdi", "eb", "rk4")])
 def test_walled_parity_fp64(pf, n, model, force, scheme):
     p = walled(n, model=model, force=force, scheme=scheme, gamma_fixed=0.2)
     po = O.params_from(p)

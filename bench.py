@@ -181,11 +181,11 @@ class ClockSampler:
 
 
 # DRAM bytes per cell per launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the 256^3 case of the finest sweep, mean of the
-# pre- and post-smoothing launches (10.7 and 15.7 B/cell); scaled to a launch
-# by the cell count. Valid for the kernel as profiled; None for every other
-# class.
-NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 13.2}
+# dram__bytes_write.sum) on the 256^3 case of the finest sweep (the TMA-staged
+# kernel), mean of the pre- and post-smoothing launches (10.9 and 15.4 B/cell);
+# scaled to a launch by the cell count. Valid for the kernel as profiled; None
+# for every other class.
+NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 13.15}
 NCU_TRAFFIC_NOTE = ("ncu DRAM bytes per cell of a 256^3 capture scaled to this grid by the cell "
                     "count: a lower bound (at 256^3 part of the reads hit the 129 MB L2)")
 

@@ -253,23 +253,70 @@ FINEST_CLASSES = ("mg_gs_level0", "cg_dir_spmv", "cg_update", "ir_residual_f64",
                   "cell_pass", "correct", "divergence", "beta0_f64", "ir_addcorr", "gamma")
 
 
-def step_roofline(prof, ncell, dim, w, ms_total, ms_host, peak):
-    """Compulsory bytes of the finest-grid kernel classes over the whole timed
-    region (algorithmic bytes per cell x cells x launches), divided by the
-    headline time: a lower bound on the step's bandwidth use (the coarse
-    multigrid levels are left out), with the share of the host-driven step
-    time those classes take."""
+def mg_levels(n, dim, coarse_cells=4096):
+    """Cells of the tiled multigrid levels (those below the single-CTA coarse
+    solve), finest first, by the library's rule: a level has a coarser one
+    while every axis is even and at least 4; the first level of at most
+    `coarse_cells` cells (else the coarsest) starts the single-CTA solve."""
+    dims = list(n[:dim])
+    allc = []
+    while True:
+        c = 1
+        for v in dims:
+            c *= v
+        allc.append(c)
+        if not all(v % 2 == 0 and v >= 4 for v in dims):
+            break
+        dims = [v // 2 for v in dims]
+    first_coarse = next((i for i, c in enumerate(allc) if c <= coarse_cells), len(allc) - 1)
+    return allc[:first_coarse]
+
+
+def coarse_class_bytes(levels, dim, w, pre=1, post=1):
+    """Algorithmic bytes of one V-cycle, per multigrid class that spans several
+    levels: the coarse tiled levels' sweeps (face arrays: pre-smoothing from
+    zero f + d faces -> x, further sweeps x + f + d faces -> x), the
+    restrictions (finest level from the cell densities on the 3D float32 path:
+    x, f, rho; coarser: x, f, d faces; plus the coarse write) and the
+    prolongations (read-add-write of the fine correction plus the coarse read),
+    each level's cells times its bytes per cell."""
+    ncoef = 1 if (dim == 3 and w == 4) else dim
+    frac = 1.0 / 2 ** dim
+    gs = sum(c * ((1 + dim + 1) * w + (pre - 1 + post) * (1 + 1 + dim + 1) * w) for c in levels[1:])
+    rs = sum(c * (((2 + (ncoef if i == 0 else dim)) * w) + w * frac) for i, c in enumerate(levels))
+    pr = sum(c * (2 * w + w * frac) for c in levels)
+    return {"mg_gs_coarse_levels": gs, "mg_restrict": rs, "mg_prolong": pr}
+
+
+def step_roofline(prof, ncell, dim, w, ms_total, ms_host, peak, levels=None, vcycles=None,
+                  pre=1, post=1):
+    """Compulsory bytes of the kernel classes over the whole timed region,
+    divided by the headline time: the finest-grid classes (algorithmic bytes
+    per cell x cells x launches) and, given the multigrid levels and the
+    number of V-cycles, the classes that span the tiled levels (their bytes
+    per V-cycle x V-cycles). The single-CTA coarse solve and the once-per-solve
+    coarsening of the coefficients are left out, so the figure is still a
+    lower bound. Also the share of the host-driven step time these classes
+    take."""
     tot_b, tot_ms = 0.0, 0.0
+    classes = []
     for cls in FINEST_CLASSES:
         if cls in prof and prof[cls][0] > 0:
             bpc = algo_bytes_per_cell(cls, dim, w, fused_stage="cell_pass" not in prof)
             tot_b += bpc * ncell * prof[cls][0]
             tot_ms += prof[cls][1]
+            classes.append(cls)
+    if levels and vcycles:
+        for cls, b in coarse_class_bytes(levels, dim, w, pre, post).items():
+            if cls in prof and prof[cls][0] > 0 and b > 0:
+                tot_b += b * vcycles
+                tot_ms += prof[cls][1]
+                classes.append(cls)
     if tot_b == 0.0 or ms_total <= 0:
         return None
     achieved = tot_b / (ms_total / 1e3) / 1e9
     return {"bound": "hbm", "bytes": tot_b, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "classes": [c for c in FINEST_CLASSES if c in prof],
+            "frac": achieved / peak, "classes": classes,
             "their_time_share": tot_ms / ms_host if ms_host > 0 else None,
             "their_bandwidth_gbs": tot_b / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else None}
 
@@ -583,7 +630,12 @@ def run_ours(args, rank, world, local_rank):
                 "share_of_step": dom_ms / ms_h if ms_h > 0 else None,
                 "timed_in": ("host-driven pass of the same steps (CUDA events around "
                              "each launch)" if args.graph else "the timed steps")}
-    step_roof = step_roofline(prof, ncell, p["dim"], w, ms, ms_h, peak)
+    pre = int(p.get("mg_pre", 0) or 1)
+    post = int(p.get("mg_post", 0) or 1)
+    levels = mg_levels(p["n"], p["dim"], int(p.get("mg_coarse_cells", 0) or 4096))
+    vcycles = prof.get("mg_coarse_vcycle", (0, 0.0))[0] if "mg_coarse_vcycle" in prof else 0
+    step_roof = step_roofline(prof, ncell, p["dim"], w, ms, ms_h, peak, levels=levels,
+                              vcycles=vcycles, pre=pre, post=post)
 
     # end to end through the C ABI: state from / to pinned host memory every step
     e2e = None

@@ -160,48 +160,48 @@ k_prolong(MGLevel<T> F, MGLevel<T> C, const CGScalars* sc) {
 
 // 3D, even nx: one thread per pair of fine cells (2I, 2I+1) of a row, which
 // share the coarse column I; the fine pair is read and written as a vector.
+// The launch is a 3D grid over (pair, row, plane), so no thread decodes its
+// cell from a linear index (integer divisions by the level's sizes).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_prolong_pairs(MGLevel<T> F, MGLevel<T> C, const CGScalars* sc) {
     if (inner_stopped(sc)) return;
     using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     const int npair = F.g.nx >> 1;
-    const int total = npair * F.g.ny * F.g.nz;   // < 2^30 (grid size limit)
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (I >= npair || j >= F.g.ny) return;
     const int cx = C.g.nx, cy = C.g.ny, cz = C.g.nz;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int row = t / npair;
-        const int I = t - row * npair;
-        const int k = row / F.g.ny, j = row - k * F.g.ny;
-        const int J0 = j >> 1, K0 = k >> 1;
-        const int J1 = wrapi(J0 + ((j & 1) ? 1 : -1), cy);
-        const int K1 = wrapi(K0 + ((k & 1) ? 1 : -1), cz);
-        const int Im = wrapi(I - 1, cx), Ip = wrapi(I + 1, cx);
-        const T* xc = C.x;
-        auto row3 = [&](int J, int K, T& m, T& c, T& p) {
-            const int base = (K * cy + J) * cx;
-            m = __ldg(xc + base + Im);
-            c = __ldg(xc + base + I);
-            p = __ldg(xc + base + Ip);
-        };
-        T m00, c00, p00, m10, c10, p10, m01, c01, p01, m11, c11, p11;
-        row3(J0, K0, m00, c00, p00);
-        row3(J1, K0, m10, c10, p10);
-        row3(J0, K1, m01, c01, p01);
-        row3(J1, K1, m11, c11, p11);
-        // even fine cell uses the -x coarse neighbour, odd the +x one
-        auto interp = [&](T nb00, T nb10, T nb01, T nb11) {
-            T v = T(0.5625) * c00 + T(0.1875) * (nb00 + c10) + T(0.0625) * nb10;
-            T v1 = T(0.5625) * c01 + T(0.1875) * (nb01 + c11) + T(0.0625) * nb11;
-            return T(0.75) * v + T(0.25) * v1;
-        };
-        const T ve = interp(m00, m10, m01, m11);
-        const T vo = interp(p00, p10, p01, p11);
-        V2* xf = reinterpret_cast<V2*>(F.x + (k * F.g.ny + j) * F.g.nx + 2 * I);
-        V2 cur = *xf;
-        cur.x += ve;
-        cur.y += vo;
-        *xf = cur;
-    }
+    const int J0 = j >> 1, K0 = k >> 1;
+    const int J1 = wrapi(J0 + ((j & 1) ? 1 : -1), cy);
+    const int K1 = wrapi(K0 + ((k & 1) ? 1 : -1), cz);
+    const int Im = wrapi(I - 1, cx), Ip = wrapi(I + 1, cx);
+    const T* xc = C.x;
+    auto row3 = [&](int J, int K, T& m, T& c, T& p) {
+        const int base = (K * cy + J) * cx;
+        m = __ldg(xc + base + Im);
+        c = __ldg(xc + base + I);
+        p = __ldg(xc + base + Ip);
+    };
+    T m00, c00, p00, m10, c10, p10, m01, c01, p01, m11, c11, p11;
+    row3(J0, K0, m00, c00, p00);
+    row3(J1, K0, m10, c10, p10);
+    row3(J0, K1, m01, c01, p01);
+    row3(J1, K1, m11, c11, p11);
+    // even fine cell uses the -x coarse neighbour, odd the +x one
+    auto interp = [&](T nb00, T nb10, T nb01, T nb11) {
+        T v = T(0.5625) * c00 + T(0.1875) * (nb00 + c10) + T(0.0625) * nb10;
+        T v1 = T(0.5625) * c01 + T(0.1875) * (nb01 + c11) + T(0.0625) * nb11;
+        return T(0.75) * v + T(0.25) * v1;
+    };
+    const T ve = interp(m00, m10, m01, m11);
+    const T vo = interp(p00, p10, p01, p11);
+    V2* xf = reinterpret_cast<V2*>(F.x + ((size_t)k * F.g.ny + j) * F.g.nx + 2 * I);
+    V2 cur = *xf;
+    cur.x += ve;
+    cur.y += vo;
+    *xf = cur;
 }
 
 // coarse face coefficients: mean of the 2^(d-1) fine faces on each coarse face
@@ -585,9 +585,13 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                 MGLevel<T> Lp = L;
                 Lp.x = cur;
                 pr->begin(KC_PROLONG);
-                k_prolong_pairs<T><<<(int)std::min<long long>((long long)L.g.ncell / 2 / kThreads + 1,
-                                                               152LL * 16),
-                                     kThreads, 0, s>>>(Lp, C, sc);
+                {
+                    const int npair = L.g.nx >> 1;
+                    const dim3 blk(npair >= 64 ? 64 : 32, npair >= 64 ? 4 : 8);
+                    const dim3 grd((npair + blk.x - 1) / blk.x, (L.g.ny + blk.y - 1) / blk.y,
+                                   L.g.nz);
+                    k_prolong_pairs<T><<<grd, blk, 0, s>>>(Lp, C, sc);
+                }
                 pr->end();
                 for (int p = 0; p < H.post; ++p) {
                     // the last level-0 sweep also forms the CG dot products

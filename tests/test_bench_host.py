@@ -41,3 +41,21 @@ def test_cpu_batch_rate_runs_the_oracle_on_a_pool(bench):
     assert len(small) == 2
     v, cores, desc = bench.cpu_batch_rate(small, steps=1, max_n=64)
     assert v > 0 and 1 <= cores <= 2 and "spawned" in desc
+
+
+def test_multilevel_classes_in_the_step_roofline(bench):
+    """The multigrid levels follow the library's halving rule, and the classes
+    that span several levels add their bytes per V-cycle times the V-cycles."""
+    assert bench.mg_levels((384, 384, 384), 3) == [384 ** 3, 192 ** 3, 96 ** 3, 48 ** 3, 24 ** 3]
+    assert bench.mg_levels((256, 256, 1), 2) == [256 ** 2, 128 ** 2]
+    lv = bench.mg_levels((64, 64, 64), 3)
+    cb = bench.coarse_class_bytes(lv, 3, 4)
+    # restriction: finest level x, f, rho (12 B) + 1/8 coarse write, then faces
+    assert cb["mg_restrict"] == lv[0] * 12.5 + lv[1] * 20.5
+    assert cb["mg_prolong"] == sum(c * 8.5 for c in lv)
+    prof = {"mg_gs_level0": (10, 2.0), "mg_restrict": (20, 1.0), "mg_prolong": (20, 1.0),
+            "mg_gs_coarse_levels": (20, 1.0), "mg_coarse_vcycle": (10, 0.5)}
+    r0 = bench.step_roofline(prof, lv[0], 3, 4, 4.0, 8.0, 100.0)
+    r1 = bench.step_roofline(prof, lv[0], 3, 4, 4.0, 8.0, 100.0, levels=lv, vcycles=10)
+    assert r1["bytes"] == r0["bytes"] + 10 * sum(cb.values())
+    assert "mg_prolong" in r1["classes"] and "mg_coarse_vcycle" not in r1["classes"]

@@ -719,6 +719,11 @@ struct ImplT final : Impl {
             int stt = h_sc->status;
             h_sc->status = 0;
             CK(cudaMemsetAsync(&sc->status, 0, sizeof(int), st));
+            // a timed-out sweep stopped the solve in the middle of a launch: blocks
+            // that started after it may have skipped a grid reduction, so its
+            // completion counter is cleared for the next solve
+            if (stt == PF_ERR_TIMEOUT)
+                CK(cudaMemsetAsync(rb.counter, 0, 4 * sizeof(unsigned int), st));
             err = stt == PF_ERR_NOT_CONVERGED ? "Poisson solve reached poisson_maxit"
                   : stt == PF_ERR_TIMEOUT
                       ? "a bounded wait of the TMA-staged sweep gave up (copies did not land)"

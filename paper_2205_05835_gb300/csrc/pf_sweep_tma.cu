@@ -27,6 +27,7 @@
 #include <cuda.h>
 
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -147,6 +148,7 @@ struct TmaArgs {
     RedBuf rb;
     CGScalars* scw;       // dots: CG scalars written by the last block
     CGScalars* st;        // status and done of the solve (timeout)
+    int stall;            // test of the bounded wait: one interior CTA expects bytes that never come
 };
 
 constexpr int CPR = HX / 4;                   // 16-byte chunks per staged row
@@ -237,7 +239,11 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
             const int z = modp(P0 + q, g.nz);
             // one tensor box (40 x 12 x 1) per array
             if (lane == 0) {
-                mbar_expect_tx(&S.bar_r[slot], PLANE_BYTES);
+                // the wait test: CTA (1, 1, 0) expects 16 bytes more than plane 2
+                // brings, so that phase never completes and its waits run out
+                const bool stall = A.stall && q == 2 && blockIdx.x == 1 && blockIdx.y == 1 &&
+                                   blockIdx.z == 0;
+                mbar_expect_tx(&S.bar_r[slot], PLANE_BYTES + (stall ? 16u : 0u));
                 tma_box(S.rho[slot], &tm_rho, i0 - OX, j0 - 2, z, &S.bar_r[slot]);
                 mbar_expect_tx(&S.bar_xf[slot], ZERO ? PLANE_BYTES : 2u * PLANE_BYTES);
                 tma_box(S.f[slot], &tm_f, i0 - OX, j0 - 2, z, &S.bar_xf[slot]);
@@ -326,6 +332,7 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
               mbar_wait(&S.bar_r[0], 0) && mbar_wait(&S.bar_r[1], 0)))
             *abort = 1;
 
+#pragma unroll 2
         for (int s = 1; s <= SMAX; ++s) {
             // plane s + 1 landed (the first colour on plane s reads s - 1 .. s + 1)
             if (s + 1 <= QMAX) {
@@ -498,6 +505,7 @@ bool encode_plane_map(CUtensorMap* m, const Dims& g, const float* base) {
 }  // namespace
 
 struct SweepTMA {
+    int stall;            // PF_TEST_SWEEP_STALL was set at creation (test of the bounded wait)
     Dims g;
     CUtensorMap rho, f, xa, xb;
     const float* rho_p;
@@ -523,6 +531,7 @@ SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, cons
     t->f_p = f;
     t->xa_p = xa;
     t->xb_p = xb;
+    t->stall = std::getenv("PF_TEST_SWEEP_STALL") != nullptr ? 1 : 0;
     if (!encode_plane_map(&t->rho, g, rho) || !encode_plane_map(&t->f, g, f) ||
         !encode_plane_map(&t->xa, g, xa) || !encode_plane_map(&t->xb, g, xb)) {
         delete t;
@@ -562,6 +571,7 @@ bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* x
     a.rb = dots ? dots->rb : RedBuf{nullptr, nullptr};
     a.scw = dots ? dots->sc : nullptr;
     a.st = const_cast<CGScalars*>(sc);
+    a.stall = t->stall;
     const Dims& g = t->g;
     int zc = 32;
     const long long cols = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);

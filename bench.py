@@ -550,6 +550,8 @@ def run_ours(args, rank, world, local_rank):
         p["mg_pre"] = p["mg_post"] = args.mg_sweeps
     if args.sweep_staging is not None:
         p["sweep_staging"] = args.sweep_staging
+    if args.sweep_tile is not None:
+        p["sweep_tile"] = args.sweep_tile
     tuned = None
     if args.autotune and args.mg_sweeps is None:
         # multigrid launch shape tuned on this grid before the timed region
@@ -731,6 +733,8 @@ def main():
                     help="pre- and post-smoothing sweeps per V-cycle (tuning; default 1)")
     ap.add_argument("--sweep-staging", type=int, default=None,
                     help="finest-level sweeps: 0 TMA-staged (the library's default), 1 cp.async")
+    ap.add_argument("--sweep-tile", type=int, default=None,
+                    help="TMA-staged sweeps' tile shape (pf_params.sweep_tile, 0 .. 3)")
     ap.add_argument("--graph", type=int, default=1,
                     help="1 (default): replay one captured CUDA graph per step (use_graph); "
                          "0: host-driven solver loops")

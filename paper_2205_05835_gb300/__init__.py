@@ -52,7 +52,7 @@ def make_params(p: dict) -> B.pf_params:
               "dt", "delta_n", "poisson_rtol", "R", "pert_amp", "bound_tol", "inner_tol"):
         setattr(q, k, float(p.get(k, 0.0) or 0.0))
     for k in ("poisson_maxit", "pert_mode", "mg_pre", "mg_post", "use_graph", "wall_y",
-              "mg_coarse_cells", "sweep_staging", "stage_kernel"):
+              "mg_coarse_cells", "sweep_staging", "stage_kernel", "sweep_tile"):
         setattr(q, k, int(p.get(k, 0) or 0))
     return q
 

@@ -8,6 +8,11 @@ converged answer (every candidate solves to the same poisson_rtol):
                      against more, shorter ones);
   mg_pre, mg_post -- red-black sweeps before and after the coarse correction
                      (cheaper V-cycles against fewer CG iterations);
+  sweep_tile      -- 3D mixed precision, tuned second with the best shape
+                     fixed: the column tile and cells per thread of the
+                     TMA-staged finest-level sweep (more warps per SM against
+                     less per-plane control per cell; smaller against larger
+                     staged halos);
   inner_tol       -- optional (tune_inner), mixed precision only, tuned
                      second with the best shape fixed: the residual reduction
                      of each float32 inner solve between float64 refinements
@@ -33,6 +38,7 @@ CANDIDATES = tuple(
     + [{"mg_coarse_cells": 4096, "mg_pre": v, "mg_post": v} for v in (8, 10)])
 
 INNER_TOLS = (1e-6, 1e-5, 1e-4, 1e-3)   # the first is the library's default
+SWEEP_TILES = (0, 1, 2, 3)              # the first is the library's default
 
 _cache: dict = {}
 
@@ -78,6 +84,14 @@ def tune(p: dict, candidates=CANDIDATES, steps: int = 2, warm: int = 1,
         times[json.dumps(c, sort_keys=True)] = 1e3 * _time_candidate(pf, p, c, steps, warm)
     best = min(times, key=times.get)
     choice = json.loads(best)
+    if int(p["dim"]) == 3 and p.get("precision") == "mixed" and "sweep_tile" not in p:
+        base_ms = times[best]
+        for tile in SWEEP_TILES[1:]:
+            c = dict(choice, sweep_tile=tile)
+            ms = 1e3 * _time_candidate(pf, p, c, steps, warm)
+            times[json.dumps(c, sort_keys=True)] = ms
+            if ms < base_ms:
+                base_ms, choice = ms, c
     if tune_inner and p.get("precision") == "mixed" and not p.get("inner_tol"):
         base_ms = times[best]
         for tol in INNER_TOLS[1:]:

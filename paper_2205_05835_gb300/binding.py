@@ -54,6 +54,7 @@ class pf_params(ctypes.Structure):
         ("mg_coarse_cells", ctypes.c_int),
         ("sweep_staging", ctypes.c_int),
         ("stage_kernel", ctypes.c_int),
+        ("sweep_tile", ctypes.c_int),
         ("reserved", ctypes.c_int * 1),
     ]
 

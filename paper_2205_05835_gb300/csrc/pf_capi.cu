@@ -209,6 +209,10 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "stage_kernel must be 0 or 1";
         return PF_ERR_INVALID;
     }
+    if (p->sweep_tile < 0 || p->sweep_tile > 3) {
+        why = "sweep_tile must be 0 .. 3";
+        return PF_ERR_INVALID;
+    }
     for (int i = 0; i < 1; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be zero"; return PF_ERR_INVALID; }
     return PF_OK;
@@ -546,7 +550,8 @@ struct ImplT final : Impl {
             prm.sweep_staging == 0 && H.first_coarse > 0) {
             tma = sweep_tma_create(g, rho0, reinterpret_cast<const float*>(H.lev[0].f),
                                    reinterpret_cast<const float*>(H.lev[0].x),
-                                   reinterpret_cast<const float*>(H.lev[0].x2));
+                                   reinterpret_cast<const float*>(H.lev[0].x2),
+                                   prm.sweep_tile);
             H.tma = tma;
         }
         return PF_OK;

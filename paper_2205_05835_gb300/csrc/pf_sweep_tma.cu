@@ -2,17 +2,18 @@
 // level (smoother weights from the cell densities rho), with every plane
 // staged into shared memory by the Tensor Memory Accelerator.
 //
-// Same arithmetic as the cp.async-staged sweep of pf_mg3d.cu, bit for bit: a
-// CTA owns a 32 x 8 column tile and marches along z; in the step for plane k
-// the first three warps update the first colour of plane k over the tile plus
-// a one-cell ring, and the last two warps update the second colour of plane
-// k - 2 from the new first-colour values of planes k - 3 .. k - 1 and write
-// both colours of plane k - 2. What differs is the staging:
+// Same per-cell arithmetic as the cp.async-staged sweep of pf_mg3d.cu, bit for
+// bit: a CTA owns a 32 x TY column tile (TY 8 or 16) and marches along z; in
+// the step for plane k one group of warps updates the first colour of plane k
+// over the tile plus a one-cell ring, and a second group updates the second
+// colour of plane k - 2 from the new first-colour values of planes k - 3 ..
+// k - 1 and writes both colours of plane k - 2; each thread takes one or two
+// cells of its colour per plane. What differs is the staging:
 //
 //  * a producer warp stages the planes, four steps ahead of their use, into
 //    rings of eight planes per array: for tiles whose halo does not cross a
 //    periodic seam one tiled tensor copy (cp.async.bulk.tensor, box
-//    40 x 12 x 1) per array, completing on the ring slot's mbarrier with the
+//    40 x (TY + 4) x 1) per array, completing on the ring slot's mbarrier with the
 //    plane's bytes; for the others 16-byte cp.async chunks with wrapped
 //    addresses, which the mbarrier tracks through cp.async.mbarrier.arrive;
 //  * the compute warps wait on those mbarriers, synchronise among themselves
@@ -42,43 +43,60 @@ namespace {
 #define PF_TMA_BOXES 1
 #endif
 
-constexpr int TX = 32, TY = 8, OX = 4;
+constexpr int TX = 32, OX = 4;                // tile width, staged columns left of it
 constexpr int HX = TX + 2 * OX;               // 40 columns of a staged plane
-constexpr int HY = TY + 4;                    // 12 rows (two-cell halo in y)
-constexpr int PLANE = HX * HY;                // 480 floats = 1920 bytes
-constexpr unsigned PLANE_BYTES = PLANE * 4u;
-constexpr int RXS = TX + 2, RYS = TY + 2;     // one-cell ring around the tile
+constexpr int RXS = TX + 2;                   // one-cell ring around the tile, x
 constexpr int RXH = RXS / 2;                  // first-colour cells per ring row (17)
-constexpr int NPL = RYS * RXH;                // first-colour cells per plane (170)
-constexpr int W1 = 96;                        // first-colour threads (3 warps, 2 cells each)
-constexpr int W2 = (TX / 2) * TY / 2;         // second-colour threads (2 warps, 2 cells each)
-constexpr int NC = W1 + W2;                   // 160 compute threads
-constexpr int NT = NC + 32;                   // + one producer warp
 constexpr int RING = 8;                       // ring planes of rho, f and x_in
 constexpr int RN = 4;                         // ring planes of the new first colour
 constexpr long long kWaitNs = 1000000000LL;   // bound of one mbarrier wait
+constexpr int CPR = HX / 4;                   // 16-byte chunks per staged row
+
+// Tile shapes: 32 x TY columns per CTA, each thread updating CPT cells of its
+// colour per plane. The staged plane and the shared-memory layout depend on
+// TY; the thread groups on both (more cells per thread: fewer warps, the
+// per-plane waits, barrier and loop control spread over more cells).
+template <int TY_, int CPT_>
+struct TileCfg {
+    static constexpr int TY = TY_;
+    static constexpr int CPT = CPT_;                     // cells per thread and plane
+    static constexpr int HY = TY + 4;                    // rows (two-cell halo in y)
+    static constexpr int PLANE = HX * HY;                // floats per staged plane
+    static constexpr unsigned PLANE_BYTES = PLANE * 4u;
+    static constexpr int RYS = TY + 2;                   // one-cell ring, y
+    static constexpr int NPL = RYS * RXH;                // first-colour cells per plane
+    static constexpr int W1 = ((NPL + 32 * CPT - 1) / (32 * CPT)) * 32;   // first-colour threads
+    static constexpr int W2 = (TX / 2) * TY / CPT;       // second-colour threads
+    static constexpr int NC = W1 + W2;                   // compute threads
+    static constexpr int NT = NC + 32;                   // + one producer warp
+    static constexpr int NCH = CPR * HY;                 // 16-byte chunks per staged plane
+    static constexpr int F_OFF = RING * PLANE;           // floats from the rho ring to the f ring
+};
 
 // Shared memory: rings of rho, f (and x_in unless the sweep starts from zero,
 // last so that a zero-start launch leaves it out), each RING planes of PLANE
 // floats; the new first-colour values; per ring slot a "full" mbarrier for
 // rho, one for f / x_in (completed by the copies' bytes) and an "empty" one
 // (the compute warps' release of the slot's plane, one arrival per warp).
-constexpr int F_OFF = RING * PLANE;           // floats from the rho ring to the f ring
-struct __align__(128) Smem {
-    float rho[RING][PLANE];
-    float f[RING][PLANE];
-    float n[RN][NPL];
+template <int TY>
+struct __align__(128) SmemT {
+    float rho[RING][TileCfg<TY, 1>::PLANE];
+    float f[RING][TileCfg<TY, 1>::PLANE];
+    float n[RN][TileCfg<TY, 1>::NPL];
     unsigned long long bar_r[RING];
     unsigned long long bar_xf[RING];
     unsigned long long bar_empty[RING];
     int abort;
     int issued;                       // last plane the producer issued
     float pad[14];
-    alignas(128) float x[RING][PLANE];
+    alignas(128) float x[RING][TileCfg<TY, 1>::PLANE];
 };
-constexpr int X_OFF = (int)(offsetof(Smem, x) / sizeof(float));   // floats from rho to x
-constexpr size_t kSmemZero = offsetof(Smem, x) + 128;            // + alignment slack
-constexpr size_t kSmemFull = sizeof(Smem) + 128;
+template <int TY>
+constexpr int x_off() { return (int)(offsetof(SmemT<TY>, x) / sizeof(float)); }   // rho -> x
+template <int TY>
+constexpr size_t smem_zero() { return offsetof(SmemT<TY>, x) + 128; }   // + alignment slack
+template <int TY>
+constexpr size_t smem_full() { return sizeof(SmemT<TY>) + 128; }
 
 __device__ __forceinline__ int modp(int a, int m) { int r = a % m; return r < 0 ? r + m : r; }
 __device__ __forceinline__ unsigned su32(const void* p) {
@@ -108,6 +126,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned pa
         : "memory");
     return ok != 0;
 }
+// Same test, but a thread whose phase is not complete is suspended until it
+// completes or about `hint_ns` nanoseconds pass (no busy polling meanwhile).
+__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long* b, unsigned parity,
+                                                    unsigned hint_ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+constexpr unsigned kSuspendNs = 20000;   // one suspended test: 20 us at most
 __device__ __forceinline__ long long global_ns() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -120,8 +153,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
     if (mbar_try_wait(b, parity)) return true;
     const long long t0 = global_ns();
     for (;;) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(b, parity)) return true;
+        if (mbar_try_wait_sleep(b, parity, kSuspendNs)) return true;
         if (global_ns() - t0 > limit) return false;
     }
 }
@@ -151,8 +183,6 @@ struct TmaArgs {
     int stall;            // test of the bounded wait: one interior CTA expects bytes that never come
 };
 
-constexpr int CPR = HX / 4;                   // 16-byte chunks per staged row
-constexpr int NCH = CPR * HY;                 // chunks per staged plane (120)
 // the barrier's pending count drops when this thread's earlier cp.async land
 __device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
@@ -165,32 +195,46 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long* b, unsign
     if (mbar_try_wait(b, parity)) return true;
     const long long t0 = global_ns();
     for (;;) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(b, parity)) return true;
+        if (mbar_try_wait_sleep(b, parity, kSuspendNs)) return true;
         if (*abort || global_ns() - t0 > kWaitNs) return false;
     }
 }
 __device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
-// barrier of the five compute warps (the producer warp runs on its own)
+// barrier of the compute warps (the producer warp runs on its own)
+template <int NC>
 __device__ __forceinline__ void compute_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
 }
 
-// Warp 5 is the producer: it issues the copies of every staged plane q (rho,
+// CTAs per SM that shared memory (228 KB, 1 KB reserved per CTA) and the
+// 2048 threads allow
+template <bool ZERO, int TY, int CPT>
+constexpr int tile_min_blocks() {
+    constexpr int by_smem = 233472 / (int)((ZERO ? smem_zero<TY>() : smem_full<TY>()) + 1024);
+    constexpr int by_threads = 2048 / TileCfg<TY, CPT>::NT;
+    return by_smem < by_threads ? by_smem : by_threads;
+}
+
+// The last warp is the producer: it issues the copies of every staged plane q (rho,
 // f and x_in together) as soon as the compute warps have released the ring
 // slot's previous plane q - RING. The compute warps release plane q at the
 // end of step q + 3 (the last step that reads it: the second colour on plane
 // q + 1 reads rho of q), so a plane is issued four steps before it is needed.
-template <bool ZERO>
-__global__ void __launch_bounds__(NT, ZERO ? 6 : 4)
+template <bool ZERO, int TY, int CPT_>
+__global__ void __launch_bounds__(TileCfg<TY, CPT_>::NT, (tile_min_blocks<ZERO, TY, CPT_>()))
 k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant__ CUtensorMap tm_f,
               const __grid_constant__ CUtensorMap tm_x, TmaArgs A, const CGScalars* sc) {
+    using C = TileCfg<TY, CPT_>;
+    constexpr int PLANE = C::PLANE, NPL = C::NPL, W1 = C::W1, W2 = C::W2, NC = C::NC;
+    constexpr int CPT = CPT_;
+    constexpr int F_OFF = C::F_OFF, X_OFF = x_off<TY>();
+    constexpr unsigned PLANE_BYTES = C::PLANE_BYTES;
     if (sc && (sc->done || sc->idone)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 128-byte aligned base (the launch reserves 128 bytes for this)
-    Smem& S = *reinterpret_cast<Smem*>(
+    SmemT<TY>& S = *reinterpret_cast<SmemT<TY>*>(
         smem_raw + ((128u - (su32(smem_raw) & 127u)) & 127u));
     float* const B = &S.rho[0][0];    // rho ring; f at B + F_OFF, x_in at B + X_OFF
     const Dims& g = A.g;
@@ -237,7 +281,7 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
                 break;
             }
             const int z = modp(P0 + q, g.nz);
-            // one tensor box (40 x 12 x 1) per array
+            // one tensor box (40 x (TY + 4) x 1) per array
             if (lane == 0) {
                 // the wait test: CTA (1, 1, 0) expects 16 bytes more than plane 2
                 // brings, so that phase never completes and its waits run out
@@ -254,16 +298,16 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
         }
     } else {
         // ---------------- compute warps ----------------
-        // fixed per-thread cells (two per thread). First colour: ring cells
-        // u = tid, tid + W1 (ring row u / 17, pair u % 17), at column offset e0
+        // fixed per-thread cells (CPT per thread). First colour: ring cells
+        // u = tid + h W1 (ring row u / 17, pair u % 17), at column offset e0
         // in its pair on even steps and 1 - e0 on odd ones. Second colour: tile
-        // cells t, t + W2 (row t / 16, pair t % 16) likewise, on the plane two
-        // behind.
+        // cells t = tid - W1 + h W2 (row t / 16, pair t % 16) likewise, on the
+        // plane two behind.
         const bool grp1 = tid < W1;
-        int ce[2], cn[2], g2[2], e0[2];
-        bool act[2];
+        int ce[CPT], cn[CPT], g2[CPT], e0[CPT];
+        bool act[CPT];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < CPT; ++h) {
             if (grp1) {
                 const int u = tid + h * W1;
                 act[h] = u < NPL;
@@ -284,42 +328,53 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
         }
         // q of the second-colour cells (fused dots), one plane ahead
         const bool want_q = A.dots && !first_it && !grp1;
-        float2 qv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        float2 qv[CPT];
+#pragma unroll
+        for (int h = 0; h < CPT; ++h) qv[h] = make_float2(0.f, 0.f);
         if (want_q && z0 < z1) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < CPT; ++h)
                 if (act[h]) qv[h] = __ldg(reinterpret_cast<const float2*>(A.q + g2[h] + 3 * sz));
         }
-        // tiles across a seam: every compute thread copies chunk tid of each
-        // staged plane (16 bytes, wrapped address; a chunk never straddles the
-        // seam: nx and the tile origin are multiples of 4), PD_E planes ahead,
-        // and the slot's full mbarriers track those copies
+        // tiles across a seam: the compute threads copy chunks tid, tid + NC,
+        // ... of each staged plane (16 bytes, wrapped address; a chunk never
+        // straddles the seam: nx and the tile origin are multiples of 4), PD_E
+        // planes ahead, and the slot's full mbarriers track those copies
         constexpr int PD_E = 4;
-        const bool has_chunk = !tma && tid < NCH;
-        int c_off = 0, c_so = 0;
-        if (has_chunk) {
-            const int r = tid / CPR, a = 4 * (tid - r * CPR);
-            c_off = modp(j0 - 2 + r, g.ny) * g.nx + modp(i0 - OX + a, g.nx);
-            c_so = r * HX + a;
+        constexpr int CH = (C::NCH + NC - 1) / NC;   // chunks per thread and array
+        bool has_chunk[CH];
+        int c_off[CH], c_so[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const int ch = tid + k * NC;
+            has_chunk[k] = !tma && ch < C::NCH;
+            const int r = ch / CPR, a = 4 * (ch - r * CPR);
+            c_off[k] = has_chunk[k] ? modp(j0 - 2 + r, g.ny) * g.nx + modp(i0 - OX + a, g.nx) : 0;
+            c_so[k] = has_chunk[k] ? r * HX + a : 0;
         }
         auto copy_plane = [&](int q) {
             if (q > QMAX) return;
             const int slot = q & (RING - 1);
-            const size_t gi = (size_t)modp(P0 + q, g.nz) * sz + c_off;
-            if (has_chunk) {
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(su32(S.rho[slot] + c_so)),
-                             "l"(A.rho + gi)
-                             : "memory");
-            }
+            const size_t gz = (size_t)modp(P0 + q, g.nz) * sz;
+#pragma unroll
+            for (int k = 0; k < CH; ++k)
+                if (has_chunk[k])
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(
+                                     su32(S.rho[slot] + c_so[k])),
+                                 "l"(A.rho + gz + c_off[k])
+                                 : "memory");
             cp_async_arrive(&S.bar_r[slot]);
-            if (has_chunk) {
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(su32(S.f[slot] + c_so)),
-                             "l"(A.f + gi)
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                if (!has_chunk[k]) continue;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(
+                                 su32(S.f[slot] + c_so[k])),
+                             "l"(A.f + gz + c_off[k])
                              : "memory");
                 if (!ZERO)
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(
-                                     su32(S.x[slot] + c_so)),
-                                 "l"(A.xin + gi)
+                                     su32(S.x[slot] + c_so[k])),
+                                 "l"(A.xin + gz + c_off[k])
                                  : "memory");
             }
             cp_async_arrive(&S.bar_xf[slot]);
@@ -341,7 +396,7 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
                 const bool w2 = mbar_wait(&S.bar_xf[(s + 1) & (RING - 1)], par);
                 if (!(w1 && w2)) *abort = 1;
             }
-            compute_sync();   // step s - 1 done by every compute warp
+            compute_sync<NC>();   // step s - 1 done by every compute warp
             if (*abort) break;
             if (!tma) copy_plane(s + PD_E);   // slot of plane s - 4, last read in step s - 1
             const int odd = s & 1;
@@ -352,7 +407,7 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
                     const int op = ((s + 1) & (RING - 1)) * PLANE;
                     float* Nn = S.n[s & (RN - 1)];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
+                    for (int h = 0; h < CPT; ++h) {
                         if (!act[h]) continue;
                         const int c = ce[h] + (e0[h] ^ odd);
                         const float* cc = B + oc + c;
@@ -385,7 +440,7 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
                 const float* Nbp = S.n[(s - 1) & (RN - 1)];
                 const bool more = s + 1 <= SMAX;   // another second-colour plane follows
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < CPT; ++h) {
                     const int s2 = e0[h] ^ odd;    // column offset of the cell in its pair
                     const int c = ce[h] + s2;
                     const float* cc = B + ob + c;
@@ -421,8 +476,8 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
                 }
             }
             if (!grp1) {
-                g2[0] += sz;
-                g2[1] += sz;
+#pragma unroll
+                for (int h = 0; h < CPT; ++h) g2[h] += sz;
             }
             // this warp is done with plane s - 3: release its ring slot
             __syncwarp();
@@ -459,14 +514,15 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
     }
 }
 
-template <bool ZERO>
+template <bool ZERO, int TY, int CPT>
 void tma_attributes() {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_sweep3d_tma<ZERO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(ZERO ? kSmemZero : kSmemFull));
-        cudaFuncSetAttribute(k_sweep3d_tma<ZERO>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             100);
+        cudaFuncSetAttribute(k_sweep3d_tma<ZERO, TY, CPT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(ZERO ? smem_zero<TY>() : smem_full<TY>()));
+        cudaFuncSetAttribute(k_sweep3d_tma<ZERO, TY, CPT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     });
 }
 
@@ -489,13 +545,13 @@ EncodeTiled encoder() {
     return fn;
 }
 
-// tensor map of one float32 array of the grid, box 40 x 12 x 1 (a staged plane)
-bool encode_plane_map(CUtensorMap* m, const Dims& g, const float* base) {
+// tensor map of one float32 array of the grid, box 40 x hy x 1 (a staged plane)
+bool encode_plane_map(CUtensorMap* m, const Dims& g, const float* base, int hy) {
     EncodeTiled fn = encoder();
     if (!fn || !base) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4u, (cuuint64_t)g.nx * g.ny * 4u};
-    const cuuint32_t box[3] = {(cuuint32_t)HX, (cuuint32_t)HY, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)HX, (cuuint32_t)hy, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -506,6 +562,8 @@ bool encode_plane_map(CUtensorMap* m, const Dims& g, const float* base) {
 
 struct SweepTMA {
     int stall;            // PF_TEST_SWEEP_STALL was set at creation (test of the bounded wait)
+    int ty;               // tile height, 8 or 16
+    int cpt;              // cells per thread and plane, 1 or 2
     Dims g;
     CUtensorMap rho, f, xa, xb;
     const float* rho_p;
@@ -522,7 +580,7 @@ bool sweep_tma_ok(const Dims& g) {
 }
 
 SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, const float* xa,
-                           const float* xb) {
+                           const float* xb, int tile) {
     if (!sweep_tma_ok(g)) return nullptr;
     SweepTMA* t = new (std::nothrow) SweepTMA;
     if (!t) return nullptr;
@@ -531,9 +589,16 @@ SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, cons
     t->f_p = f;
     t->xa_p = xa;
     t->xb_p = xb;
+    // tile shapes (pf_params.sweep_tile): 0 32 x 8, one cell per thread;
+    // 1 32 x 8, two; 2 32 x 16, two; 3 32 x 16, one. 32 x 16 tiles need a
+    // staged plane's 20 rows within the grid (else the 32 x 8 shape).
+    const bool tall = (tile == 2 || tile == 3) && g.ny >= TileCfg<16, 1>::HY;
+    t->ty = tall ? 16 : 8;
+    t->cpt = (tile == 1 || tile == 2) ? 2 : 1;
     t->stall = std::getenv("PF_TEST_SWEEP_STALL") != nullptr ? 1 : 0;
-    if (!encode_plane_map(&t->rho, g, rho) || !encode_plane_map(&t->f, g, f) ||
-        !encode_plane_map(&t->xa, g, xa) || !encode_plane_map(&t->xb, g, xb)) {
+    const int hy = t->ty + 4;
+    if (!encode_plane_map(&t->rho, g, rho, hy) || !encode_plane_map(&t->f, g, f, hy) ||
+        !encode_plane_map(&t->xa, g, xa, hy) || !encode_plane_map(&t->xb, g, xb, hy)) {
         delete t;
         return nullptr;
     }
@@ -542,15 +607,52 @@ SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, cons
 
 void sweep_tma_destroy(SweepTMA* t) { delete t; }
 
-void sweep_tma_prepare() {
-    tma_attributes<true>();
-    tma_attributes<false>();
+int sweep_tma_tile(const SweepTMA* t) {
+    if (!t) return -1;
+    return t->ty == 16 ? (t->cpt == 2 ? 2 : 3) : (t->cpt == 2 ? 1 : 0);
 }
+
+void sweep_tma_prepare() {
+    tma_attributes<true, 8, 2>();
+    tma_attributes<false, 8, 2>();
+    tma_attributes<true, 8, 1>();
+    tma_attributes<false, 8, 1>();
+    tma_attributes<true, 16, 2>();
+    tma_attributes<false, 16, 2>();
+    tma_attributes<true, 16, 1>();
+    tma_attributes<false, 16, 1>();
+}
+
+namespace {
+template <int TY, int CPT>
+void launch_tiles(const SweepTMA* t, const CUtensorMap* tx, TmaArgs& a, bool zero,
+                  const SweepDots* dots, bool* ok, const CGScalars* sc, cudaStream_t s) {
+    const Dims& g = t->g;
+    int zc = 32;
+    const long long cols = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    while (zc > 2 && cols * ((g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
+    if (zc == 32 && cols * ((g.nz + 63) / 64) >= 8 * 152) zc = 64;
+    a.zc = zc;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + zc - 1) / zc);
+    *ok = !(dots && 2LL * grid.x * grid.y * grid.z > (long long)kRedPart);
+    if (!*ok) return;
+    if (zero) {
+        tma_attributes<true, TY, CPT>();
+        k_sweep3d_tma<true, TY, CPT>
+            <<<grid, TileCfg<TY, CPT>::NT, smem_zero<TY>(), s>>>(t->rho, t->f, *tx, a, sc);
+    } else {
+        tma_attributes<false, TY, CPT>();
+        k_sweep3d_tma<false, TY, CPT>
+            <<<grid, TileCfg<TY, CPT>::NT, smem_full<TY>(), s>>>(t->rho, t->f, *tx, a, sc);
+    }
+}
+}  // namespace
 
 bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* xin, float* xout,
                       const SweepDots* dots, int first_color, const CGScalars* sc,
                       cudaStream_t s) {
     if (!t || L.f != t->f_p) return false;
+    if (sc == nullptr) return false;   // the timeout status needs the solve's scalars
     const CUtensorMap* tx = &t->xa;   // unused for a zero start
     if (xin != nullptr) {
         if (xin == t->xa_p) tx = &t->xa;
@@ -572,23 +674,17 @@ bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* x
     a.scw = dots ? dots->sc : nullptr;
     a.st = const_cast<CGScalars*>(sc);
     a.stall = t->stall;
-    const Dims& g = t->g;
-    int zc = 32;
-    const long long cols = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-    while (zc > 2 && cols * ((g.nz + zc - 1) / zc) < 8 * 152) zc >>= 1;
-    if (zc == 32 && cols * ((g.nz + 63) / 64) >= 8 * 152) zc = 64;
-    a.zc = zc;
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + zc - 1) / zc);
-    if (dots && 2LL * grid.x * grid.y * grid.z > (long long)kRedPart) return false;
-    if (sc == nullptr) return false;   // the timeout status needs the solve's scalars
-    if (xin == nullptr) {
-        tma_attributes<true>();
-        k_sweep3d_tma<true><<<grid, NT, kSmemZero, s>>>(t->rho, t->f, *tx, a, sc);
-    } else {
-        tma_attributes<false>();
-        k_sweep3d_tma<false><<<grid, NT, kSmemFull, s>>>(t->rho, t->f, *tx, a, sc);
-    }
-    return true;
+    bool ok = false;
+    const bool zero = xin == nullptr;
+    if (t->ty == 16 && t->cpt == 2)
+        launch_tiles<16, 2>(t, tx, a, zero, dots, &ok, sc, s);
+    else if (t->ty == 16)
+        launch_tiles<16, 1>(t, tx, a, zero, dots, &ok, sc, s);
+    else if (t->cpt == 2)
+        launch_tiles<8, 2>(t, tx, a, zero, dots, &ok, sc, s);
+    else
+        launch_tiles<8, 1>(t, tx, a, zero, dots, &ok, sc, s);
+    return ok;
 }
 
 }  // namespace pf

@@ -76,6 +76,10 @@ def test_workspace_size_and_validation(pf):
     bad.stage_kernel = 2
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
+    bad = pf.make_params(I.static_drop_64())
+    bad.sweep_tile = 4
+    with pytest.raises(pf.PFError):
+        pf.pf_workspace_size(bad)
 
 
 def test_init_rejects_bad_workspace_without_touching_the_gpu(pf):

@@ -59,3 +59,21 @@ def test_tune_picks_a_candidate_and_caches(pf):
     sim.step(3)
     assert sim.diagnostics()["poisson_relres"] < 1e-10
     sim.close()
+
+
+def test_tune_picks_a_sweep_tile_on_a_3d_mixed_grid(pf):
+    """3D mixed precision: the tile shape of the TMA-staged finest sweep is tuned
+    after the multigrid shape; every tile gives a converged solve."""
+    from paper_2205_05835_gb300 import autotune
+
+    p = I.small_case(dim=3, n=64, precision="mixed", poisson_rtol=1e-10)
+    cands = autotune.CANDIDATES[:2]
+    r = autotune.tune(p, candidates=cands, steps=1, warm=1)
+    assert not r["cached"]
+    assert len(r["ms_per_step"]) == len(cands) + len(autotune.SWEEP_TILES) - 1
+    assert r["choice"].get("sweep_tile", 0) in autotune.SWEEP_TILES
+    for tile in autotune.SWEEP_TILES:
+        sim = pf.Simulation(dict(autotune.apply(p, r), sweep_tile=tile))
+        sim.step(2)
+        assert sim.diagnostics()["poisson_relres"] < 1e-10
+        sim.close()

@@ -390,9 +390,15 @@ def test_rk4_shear_mode_amplification_gpu(pf, dim, n, precision, tol):
 @pytest.mark.parametrize("n", [(128, 32, 16), (96, 48, 32), (64, 64, 64), (40, 24, 16)])
 def test_tma_staged_sweep_matches_cp_async_sweep(pf, n):
     """The finest-level sweep staged by the TMA (tensor boxes for tiles away from
-    the periodic seams, bulk row copies across them) computes exactly what the
-    cp.async-staged sweep computes: the same solution bit for bit and the same
-    iteration count, and whole mixed steps agree bit for bit."""
+    the periodic seams, cp.async chunks tracked by the mbarriers across them)
+    computes exactly what the cp.async-staged sweep computes: with the same 32 x 8
+    tiles and two cells per thread the same solution bit for bit and the same
+    iteration count, and whole mixed steps agree bit for bit. With the other tile
+    shapes (one cell per thread, 32 x 16 tiles) every cell's update is the same
+    arithmetic but the fused r.z and z.q dot products sum their partials in
+    another order, so the solves agree to that rounding (the
+    velocities after two steps, a few 1e-6 at most here, to 1e-4 of their
+    maximum: about 1e-10 absolute)."""
     p = I.small_case(dim=3, n=n[0], rho_in=10.0, rho_out=1.0, precision="mixed",
                      poisson_rtol=1e-12, poisson_maxit=200)
     p["n"] = n
@@ -402,17 +408,25 @@ def test_tma_staged_sweep_matches_cp_async_sweep(pf, n):
     rhs = I.noise(g.shape, 17) - 0.5
     rhs -= rhs.mean()
     out = []
-    for staging in (0, 1):
-        sim = pf.Simulation(dict(p, sweep_staging=staging), phi0=phi)
+    for knobs in ({"sweep_staging": 1}, {"sweep_staging": 0, "sweep_tile": 1},
+                  {"sweep_staging": 0, "sweep_tile": 0}, {"sweep_staging": 0, "sweep_tile": 2},
+                  {"sweep_staging": 0, "sweep_tile": 3}):
+        sim = pf.Simulation(dict(p, **knobs), phi0=phi)
         x, it, relres, st = sim.poisson_solve(rhs)
         assert st == 0 and relres <= 1e-12
         sim.step(2)
         out.append((x, it, {c: sim.field(c) for c in ("phi", "u", "v", "w", "p")}))
         sim.close()
-    np.testing.assert_array_equal(out[0][0], out[1][0])
-    assert out[0][1] == out[1][1]
-    for c in out[0][2]:
-        np.testing.assert_array_equal(out[0][2][c], out[1][2][c])
+    ref, tma8 = out[:2]
+    np.testing.assert_array_equal(tma8[0], ref[0])
+    assert tma8[1] == ref[1]
+    for c in ref[2]:
+        np.testing.assert_array_equal(tma8[2][c], ref[2][c])
+    for tall in out[2:]:
+        assert abs(tall[1] - ref[1]) <= 1
+        assert rel(tall[0], ref[0]) < 1e-8
+        for c in ref[2]:
+            assert rel(tall[2][c], ref[2][c]) < (1e-4 if c in "uvw" else 1e-6), c
 
 
 @pytest.mark.parametrize("model", ["cdi", "acdi"])

@@ -518,7 +518,7 @@ __device__ __forceinline__ float rcp_fast(float x) {
 }
 
 template <bool RHO>
-__global__ void __launch_bounds__(256) k_dir3d_reg(DirRegArgs A) {
+__global__ void __launch_bounds__(256, 5) k_dir3d_reg(DirRegArgs A) {
     CGScalars* sc = A.sc;
     if (sc->done || sc->idone) return;
     const Dims& g = A.g;
@@ -699,7 +699,7 @@ struct IRArgs {
     CGScalars* sc;
 };
 
-__global__ void __launch_bounds__(256) k_ir_residual3d(IRArgs A) {
+__global__ void __launch_bounds__(256, 6) k_ir_residual3d(IRArgs A) {
     CGScalars* sc = A.sc;
     if (!A.first && sc->done) return;
     const Dims& g = A.g;

@@ -517,8 +517,14 @@ __device__ __forceinline__ float rcp_fast(float x) {
     return r;
 }
 
+// Fetch the 128-byte line holding p into L2 without waiting for it.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+constexpr int kColumnAhead = 4;   // planes between an L2 prefetch and its use (column marches)
+
 template <bool RHO>
-__global__ void __launch_bounds__(256, 5) k_dir3d_reg(DirRegArgs A) {
+__global__ void __launch_bounds__(256, 4) k_dir3d_reg(DirRegArgs A) {
     CGScalars* sc = A.sc;
     if (sc->done || sc->idone) return;
     const Dims& g = A.g;
@@ -615,9 +621,19 @@ __global__ void __launch_bounds__(256, 5) k_dir3d_reg(DirRegArgs A) {
             bz_c = bz_n;
             if (RHO) r_c = L.bzn;
         };
+        // L2 prefetch of the warp's row (32 columns) of z, p_old and rho (RHO)
+        // or z, p_old and the z faces, kColumnAhead planes ahead: lane l < 6
+        // takes array l % 3 of plane (l / 3) of the round
+        const int lane = threadIdx.x % 32;
+        const int pf_arr = lane % 3, pf_dz = lane / 3;
+        const float* pf_ptr = (pf_arr == 0 ? zp : pf_arr == 1 ? po : (RHO ? rp : bzp)) +
+                              (j * sy + blockIdx.x * 32);
+        const bool pf_on = lane < 6 && !(pf_arr == 1 && first);
         // two planes per round: all loads of both before the arithmetic
         int k = z0;
         for (; k + 1 < z1; k += 2) {
+            const int kq = k + kColumnAhead + pf_dz;
+            if (pf_on && kq <= z1) prefetch_l2(pf_ptr + (size_t)(kq >= g.nz ? kq - g.nz : kq) * sz);
             Ld a, b;
             load(k, a);
             load(k + 1, b);
@@ -770,7 +786,9 @@ __global__ void __launch_bounds__(256, 6) k_ir_residual3d(IRArgs A) {
             cl = L.pl;
             bz_c = L.bzn;
         };
-        // two planes per round: all loads of both before the arithmetic
+        // two planes per round: all loads of both before the arithmetic (an L2
+        // prefetch of later planes, as in the direction kernel, measured
+        // slower here: the registers it takes cost resident CTAs)
         int k = z0;
         for (; k + 1 < z1; k += 2) {
             Ld a, b;
@@ -853,8 +871,10 @@ __device__ __forceinline__ float2 rcp2(float2 a, float2 b) {
     return make_float2(rcp_fast(a.x + b.x), rcp_fast(a.y + b.y));
 }
 
+constexpr int kRestrictAhead = 3;   // fine planes between an L2 prefetch and its use
+
 template <bool RHO>
-__global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CGScalars* sc) {
+__global__ void __launch_bounds__(256, 5) k_restrict3d_reg(RestrictArgs A, const CGScalars* sc) {
     if (sc->done || sc->idone) return;
     const int I = blockIdx.x * 32 + threadIdx.x % 32;
     const int J = blockIdx.y * 8 + threadIdx.x / 32;
@@ -894,10 +914,25 @@ __global__ void __launch_bounds__(256) k_restrict3d_reg(RestrictArgs A, const CG
         zc0 = pair(bz, kb + r0 + i);
         zc1 = pair(bz, kb + r1 + i);
     }
+    // L2 prefetch of the warp's two fine rows of x, f (and rho) kRestrictAhead
+    // planes ahead: lane l < 12 takes array l / 4, row (l / 2) % 2 and the
+    // 128-byte half l % 2 of the warp's 256-byte row segment
+    const int lane = threadIdx.x % 32;
+    const int i_w = 2 * (blockIdx.x * 32);           // first fine column of the warp
+    const int pf_arr = lane >> 2, pf_row = (lane >> 1) & 1, pf_half = lane & 1;
+    const float* pf_base = pf_arr == 0 ? x : pf_arr == 1 ? f : rho;
+    const int pf_col = i_w + 32 * pf_half;
+    const bool pf_on = lane < (RHO ? 12 : 8) && pf_col < nx;
+    const int pf_off = (pf_row ? r1 : r0) + pf_col;
+    const int k_last = 2 * K1;                        // one past the last fine plane read
     for (int K = K0; K < K1; ++K) {
         float s = 0.f;
 #pragma unroll
         for (int h = 0; h < 2; ++h, ++k) {
+            if (pf_on && k + kRestrictAhead <= k_last) {
+                const int kq = k + kRestrictAhead;
+                prefetch_l2(pf_base + (size_t)(kq >= nz ? kq - nz : kq) * sz + pf_off);
+            }
             const int kp = k + 1 == nz ? 0 : k + 1;
             const int kpb = kp * sz;
             const float2 p0 = pair(x, kpb + r0 + i), p1 = pair(x, kpb + r1 + i);

@@ -10,7 +10,10 @@
 // shared-memory rings by cp.async, one step ahead of their use. The step for
 // plane k
 //   (1) forms n (of phi, or of psi for ACDI), mu and psi of plane k + 1 on
-//       the tile plus a one-cell ring (they need phi of planes k .. k + 2);
+//       the tile plus a one-cell ring (they need phi of planes k .. k + 2;
+//       ACDI: psi of plane k + 2 is formed here on the tile plus a two-cell
+//       ring, once per cell, into a ring of four psi planes that the
+//       normals of the next steps and the face sharpening read);
 //   (2) evaluates the phase-field and momentum right-hand sides of plane k
 //       from the staged phi, u and the derived fields of planes k - 1 .. k + 1
 //       and applies the RK stage update.
@@ -31,14 +34,16 @@ constexpr int HY = TY + 2 * OY;               // 12 rows
 constexpr int PL = HX * HY;                   // 480 floats per plane
 constexpr int CPR = HX / 4, NCH = CPR * HY;   // 16-byte chunks per row / plane
 constexpr int RP = 5, RU = 4, RD = 3;         // ring planes: phi, each u, each derived field
+constexpr int RQ = 4;                         // ring planes of the ACDI psi
 constexpr int NR = (TX + 2) * (TY + 2);       // derived-field cells (tile + one-cell ring): 340
+constexpr int NR2 = (TX + 4) * (TY + 4);      // psi cells (tile + two-cell ring): 432
 
 struct Smem {
     float phi[RP][PL];
     float u[3][RU][PL];
     float n[3][RD][PL];
     float mu[RD][PL];
-    float psi[RD][PL];
+    float psi[RQ][PL];
 };
 
 struct FusedArgs {
@@ -99,6 +104,19 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
     auto sp = [&](int k) { return modp(k - z0, RP); };
     auto su = [&](int k) { return modp(k - z0, RU); };
     auto sd = [&](int k) { return modp(k - z0, RD); };
+    auto sq = [&](int k) { return modp(k - z0, RQ); };
+    // ACDI: psi of plane k on the tile plus a two-cell ring, once per cell
+    // (the normals of plane k - 1 read it at in-plane neighbours, those of
+    // k - 2 and k at the own column)
+    auto psi_plane = [&](int k) {
+        const float* P = S.phi[sp(k)];
+        float* Q = S.psi[sq(k)];
+        for (int c = tid; c < NR2; c += NTH) {
+            const int ry = c / (TX + 4), rx = c - ry * (TX + 4);
+            const int o = (ry + OY - 2) * HX + rx + OX - 2;
+            Q[o] = acdi_psi(P[o], eps);
+        }
+    };
 
     // prologue: phi of planes z0 - 2 .. z0, u of plane z0 - 1
     stage_plane(io.phi_s, S.phi[sp(z0 - 2)], z0 - 2);
@@ -110,6 +128,13 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
 
     // the thread's own cell in a staged plane
     const int cs = (ty + OY) * HX + tx + OX;
+    if (acdi) {
+        // psi of planes z0 - 2 and z0 - 1 (the first step forms z0)
+        cp_wait_all();
+        __syncthreads();
+        psi_plane(z0 - 2);
+        psi_plane(z0 - 1);
+    }
 
     for (int k = z0 - 2; k < z1; ++k) {
         cp_wait_all();
@@ -123,6 +148,8 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
         cp_commit();
 
         // (1) derived fields of plane k + 1 on the tile plus a one-cell ring
+        // (ACDI: with psi of plane k + 2 on the tile plus a two-cell ring; psi
+        // of the planes k and k + 1 was formed by the two steps before)
         if (k + 1 <= z1) {
             const float* P0 = S.phi[sp(k)];
             const float* P1 = S.phi[sp(k + 1)];
@@ -131,19 +158,28 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
             float* N1 = S.n[1][sd(k + 1)];
             float* N2 = S.n[2][sd(k + 1)];
             float* MU = S.mu[sd(k + 1)];
-            float* PS = S.psi[sd(k + 1)];
-            for (int c = tid; c < NR; c += NTH) {
-                const int ry = c / (TX + 2), rx = c - ry * (TX + 2);
-                const int o = (ry + OY - 1) * HX + rx + OX - 1;
+            const float* Q0 = S.psi[sq(k)];
+            const float* Q1 = S.psi[sq(k + 1)];
+            float* Q2 = S.psi[sq(k + 2)];
+            for (int c = tid; c < (acdi ? NR2 : NR); c += NTH) {
+                int o;
+                if (acdi) {
+                    const int ry = c / (TX + 4), rx = c - ry * (TX + 4);
+                    o = (ry + OY - 2) * HX + rx + OX - 2;
+                    Q2[o] = acdi_psi(P2[o], eps);
+                    if (ry < 1 || ry > TY + 2 || rx < 1 || rx > TX + 2) continue;   // outer ring
+                } else {
+                    const int ry = c / (TX + 2), rx = c - ry * (TX + 2);
+                    o = (ry + OY - 1) * HX + rx + OX - 1;
+                }
                 const float pc = P1[o];
                 const float xm = P1[o - 1], xp = P1[o + 1], ym = P1[o - HX], yp = P1[o + HX];
                 const float zm = P0[o], zp = P2[o];
                 float g0, g1, g2;
                 if (acdi) {
-                    g0 = (acdi_psi(xp, eps) - acdi_psi(xm, eps)) * inv2h;
-                    g1 = (acdi_psi(yp, eps) - acdi_psi(ym, eps)) * inv2h;
-                    g2 = (acdi_psi(zp, eps) - acdi_psi(zm, eps)) * inv2h;
-                    PS[o] = acdi_psi(pc, eps);
+                    g0 = (Q1[o + 1] - Q1[o - 1]) * inv2h;
+                    g1 = (Q1[o + HX] - Q1[o - HX]) * inv2h;
+                    g2 = (Q2[o] - Q0[o]) * inv2h;
                 } else {
                     g0 = (xp - xm) * inv2h;
                     g1 = (yp - ym) * inv2h;
@@ -179,7 +215,7 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
             }
         }
         const float* Mp[3] = {S.mu[sd(k - 1)], S.mu[sd(k)], S.mu[sd(k + 1)]};
-        const float* Qp[3] = {S.psi[sd(k - 1)], S.psi[sd(k)], S.psi[sd(k + 1)]};
+        const float* Qp[3] = {S.psi[sq(k - 1)], S.psi[sq(k)], S.psi[sq(k + 1)]};
         // value of a plane set at the offset (dx, dy, dz) from the own cell
         auto at = [&](const float* const* pl, int dx, int dy, int dz) {
             return pl[1 + dz][cs + dx + dy * HX];

@@ -734,7 +734,7 @@ def main():
     ap.add_argument("--sweep-staging", type=int, default=None,
                     help="finest-level sweeps: 0 TMA-staged (the library's default), 1 cp.async")
     ap.add_argument("--sweep-tile", type=int, default=None,
-                    help="TMA-staged sweeps' tile shape (pf_params.sweep_tile, 0 .. 3)")
+                    help="TMA-staged sweeps' tile shape (pf_params.sweep_tile, 0 .. 4)")
     ap.add_argument("--graph", type=int, default=1,
                     help="1 (default): replay one captured CUDA graph per step (use_graph); "
                          "0: host-driven solver loops")

@@ -135,11 +135,12 @@ typedef struct {
                              round trip of the derived fields; n[0] % 4 == 0, n[0] >= 40,
                              n[1] >= 12); 1: a cell-pass kernel writes them to the workspace
                              and the stage kernel reads them back. Same arithmetic. */
-    int sweep_tile;       /* TMA-staged finest sweeps, the CTA's column tile and cells per
-                             thread: 0 (default) 32 x 8, one; 1: 32 x 8, two; 2: 32 x 16,
-                             two; 3: 32 x 16, one (32 x 16 needs n[1] >= 20, else 32 x 8).
-                             A tuning knob: every cell gets the same update; only the fused
-                             dot products' partial sums are grouped differently. */
+    int sweep_tile;       /* TMA-staged finest sweeps, the CTA's column tile and the cells per
+                             thread of zero-start / other sweeps: 0 (default) 32 x 8, two /
+                             one; 1: 32 x 8, two; 2: 32 x 16, two; 3: 32 x 16, one; 4: 32 x 8,
+                             one (32 x 16 needs n[1] >= 20, else 32 x 8). A tuning knob: every
+                             cell gets the same update; only the fused dot products' partial
+                             sums are grouped differently. */
     int reserved[1];      /* must be zero */
 } pf_params;
 

@@ -38,7 +38,7 @@ CANDIDATES = tuple(
     + [{"mg_coarse_cells": 4096, "mg_pre": v, "mg_post": v} for v in (8, 10)])
 
 INNER_TOLS = (1e-6, 1e-5, 1e-4, 1e-3)   # the first is the library's default
-SWEEP_TILES = (0, 1, 2, 3)              # the first is the library's default
+SWEEP_TILES = (0, 1, 2, 3, 4)           # the first is the library's default
 
 _cache: dict = {}
 

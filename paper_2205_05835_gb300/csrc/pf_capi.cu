@@ -209,8 +209,8 @@ pf_status validate(const pf_params* p, std::string& why) {
         why = "stage_kernel must be 0 or 1";
         return PF_ERR_INVALID;
     }
-    if (p->sweep_tile < 0 || p->sweep_tile > 3) {
-        why = "sweep_tile must be 0 .. 3";
+    if (p->sweep_tile < 0 || p->sweep_tile > 4) {
+        why = "sweep_tile must be 0 .. 4";
         return PF_ERR_INVALID;
     }
     for (int i = 0; i < 1; ++i)

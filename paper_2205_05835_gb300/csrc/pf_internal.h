@@ -170,12 +170,12 @@ struct SweepDots {
 // of level 0 (host object, nullptr when not eligible or the driver lacks the
 // encoder), and the launch (false: not launched, use launch_sweep3d). A
 // bounded wait that gives up latches PF_ERR_TIMEOUT in the solve's scalars.
-// tile: the tile shape of pf_params.sweep_tile (0 .. 3).
+// tile: the tile shape of pf_params.sweep_tile (0 .. 4).
 bool sweep_tma_ok(const Dims& g);
 SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, const float* xa,
                            const float* xb, int tile);
 void sweep_tma_destroy(SweepTMA* t);
-int sweep_tma_tile(const SweepTMA* t);   // shape in use, 0 .. 3 (-1: no object)
+int sweep_tma_tile(const SweepTMA* t);   // shape code in use, 0 .. 4 (-1: no object)
 void sweep_tma_prepare();
 bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* xin, float* xout,
                       const SweepDots* dots, int first_color, const CGScalars* sc,

@@ -563,7 +563,9 @@ bool encode_plane_map(CUtensorMap* m, const Dims& g, const float* base, int hy) 
 struct SweepTMA {
     int stall;            // PF_TEST_SWEEP_STALL was set at creation (test of the bounded wait)
     int ty;               // tile height, 8 or 16
-    int cpt;              // cells per thread and plane, 1 or 2
+    int cpt_zero;         // cells per thread and plane of zero-start sweeps, 1 or 2
+    int cpt_full;         // the same for sweeps from a given x_in
+    int tile;             // the pf_params.sweep_tile code
     Dims g;
     CUtensorMap rho, f, xa, xb;
     const float* rho_p;
@@ -589,12 +591,15 @@ SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, cons
     t->f_p = f;
     t->xa_p = xa;
     t->xb_p = xb;
-    // tile shapes (pf_params.sweep_tile): 0 32 x 8, one cell per thread;
-    // 1 32 x 8, two; 2 32 x 16, two; 3 32 x 16, one. 32 x 16 tiles need a
-    // staged plane's 20 rows within the grid (else the 32 x 8 shape).
+    // tile shapes (pf_params.sweep_tile), cells per thread of zero-start /
+    // other sweeps: 0 32 x 8, two / one; 1 32 x 8, two; 2 32 x 16, two;
+    // 3 32 x 16, one; 4 32 x 8, one. 32 x 16 tiles need a staged plane's 20
+    // rows within the grid (else 32 x 8).
     const bool tall = (tile == 2 || tile == 3) && g.ny >= TileCfg<16, 1>::HY;
     t->ty = tall ? 16 : 8;
-    t->cpt = (tile == 1 || tile == 2) ? 2 : 1;
+    t->tile = tile;
+    t->cpt_zero = (tile == 3 || tile == 4) ? 1 : 2;
+    t->cpt_full = (tile == 1 || tile == 2) ? 2 : 1;
     t->stall = std::getenv("PF_TEST_SWEEP_STALL") != nullptr ? 1 : 0;
     const int hy = t->ty + 4;
     if (!encode_plane_map(&t->rho, g, rho, hy) || !encode_plane_map(&t->f, g, f, hy) ||
@@ -607,10 +612,7 @@ SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, cons
 
 void sweep_tma_destroy(SweepTMA* t) { delete t; }
 
-int sweep_tma_tile(const SweepTMA* t) {
-    if (!t) return -1;
-    return t->ty == 16 ? (t->cpt == 2 ? 2 : 3) : (t->cpt == 2 ? 1 : 0);
-}
+int sweep_tma_tile(const SweepTMA* t) { return t ? t->tile : -1; }
 
 void sweep_tma_prepare() {
     tma_attributes<true, 8, 2>();
@@ -676,11 +678,12 @@ bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* x
     a.stall = t->stall;
     bool ok = false;
     const bool zero = xin == nullptr;
-    if (t->ty == 16 && t->cpt == 2)
+    const int cpt = zero ? t->cpt_zero : t->cpt_full;
+    if (t->ty == 16 && cpt == 2)
         launch_tiles<16, 2>(t, tx, a, zero, dots, &ok, sc, s);
     else if (t->ty == 16)
         launch_tiles<16, 1>(t, tx, a, zero, dots, &ok, sc, s);
-    else if (t->cpt == 2)
+    else if (cpt == 2)
         launch_tiles<8, 2>(t, tx, a, zero, dots, &ok, sc, s);
     else
         launch_tiles<8, 1>(t, tx, a, zero, dots, &ok, sc, s);

@@ -77,7 +77,7 @@ def test_workspace_size_and_validation(pf):
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
     bad = pf.make_params(I.static_drop_64())
-    bad.sweep_tile = 4
+    bad.sweep_tile = 5
     with pytest.raises(pf.PFError):
         pf.pf_workspace_size(bad)
 

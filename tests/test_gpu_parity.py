@@ -394,7 +394,7 @@ def test_tma_staged_sweep_matches_cp_async_sweep(pf, n):
     computes exactly what the cp.async-staged sweep computes: with the same 32 x 8
     tiles and two cells per thread the same solution bit for bit and the same
     iteration count, and whole mixed steps agree bit for bit. With the other tile
-    shapes (one cell per thread, 32 x 16 tiles) every cell's update is the same
+    shapes (one cell per thread in some sweeps, 32 x 16 tiles) every cell's update is the same
     arithmetic but the fused r.z and z.q dot products sum their partials in
     another order, so the solves agree to that rounding (the
     velocities after two steps, a few 1e-6 at most here, to 1e-4 of their
@@ -410,7 +410,7 @@ def test_tma_staged_sweep_matches_cp_async_sweep(pf, n):
     out = []
     for knobs in ({"sweep_staging": 1}, {"sweep_staging": 0, "sweep_tile": 1},
                   {"sweep_staging": 0, "sweep_tile": 0}, {"sweep_staging": 0, "sweep_tile": 2},
-                  {"sweep_staging": 0, "sweep_tile": 3}):
+                  {"sweep_staging": 0, "sweep_tile": 3}, {"sweep_staging": 0, "sweep_tile": 4}):
         sim = pf.Simulation(dict(p, **knobs), phi0=phi)
         x, it, relres, st = sim.poisson_solve(rhs)
         assert st == 0 and relres <= 1e-12

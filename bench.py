@@ -185,7 +185,9 @@ class ClockSampler:
 # kernel), mean of the pre- and post-smoothing launches (10.9 and 15.4 B/cell);
 # scaled to a launch by the cell count. Valid for the kernel as profiled; None
 # for every other class.
-NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 13.15}
+# mean of the zero-start and post-smoothing launches of the library's default
+# finest sweep (TMA staging, sweep_tile 0)
+NCU_TRAFFIC_PER_CELL = {"mg_gs_level0": 13.09}
 NCU_TRAFFIC_NOTE = ("ncu DRAM bytes per cell of a 256^3 capture scaled to this grid by the cell "
                     "count: a lower bound (at 256^3 part of the reads hit the 129 MB L2)")
 
@@ -625,7 +627,9 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (NCU_TRAFFIC_PER_CELL[dom] * ncell
                             if dom in NCU_TRAFFIC_PER_CELL and p["dim"] == 3
-                            and p.get("precision") == "mixed" else None),
+                            and p.get("precision") == "mixed"
+                            and not p.get("sweep_tile") and not p.get("sweep_staging")
+                            else None),
                 "traffic_note": (NCU_TRAFFIC_NOTE if dom in NCU_TRAFFIC_PER_CELL else None),
                 "algo_bytes_per_launch": bpc * ncell,
                 "avg_launch_us": avg_s * 1e6,

@@ -491,7 +491,8 @@ def fp64_baseline(pf, torch, p, stream, local_rank, graph, steps=3):
         mix = pf.Simulation(dict(p, use_graph=use_graph), stream=stream)
     phi0 = mix.field("phi")
     mix.step(1 + steps)
-    mfields = {c: mix.field(c) for c in ("phi", "u", "v", "w", "p")}
+    names = ("phi", "u", "v", "w", "p") if int(p["dim"]) == 3 else ("phi", "u", "v", "p")
+    mfields = {c: mix.field(c) for c in names}
     mix.close()
     del mix
     torch.cuda.empty_cache()

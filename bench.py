@@ -274,18 +274,24 @@ def mg_levels(n, dim, coarse_cells=4096):
     return allc[:first_coarse]
 
 
+DENSITY_LEVELS = 1   # coarse levels rediscretised from cell densities (3D float32 path)
+
+
 def coarse_class_bytes(levels, dim, w, pre=1, post=1):
     """Algorithmic bytes of one V-cycle, per multigrid class that spans several
-    levels: the coarse tiled levels' sweeps (face arrays: pre-smoothing from
-    zero f + d faces -> x, further sweeps x + f + d faces -> x), the
-    restrictions (finest level from the cell densities on the 3D float32 path:
-    x, f, rho; coarser: x, f, d faces; plus the coarse write) and the
+    levels: the coarse tiled levels' sweeps (pre-smoothing from zero: f and
+    the coefficients -> x; further sweeps x, f and the coefficients -> x), the
+    restrictions (x, f and the coefficients, plus the coarse write) and the
     prolongations (read-add-write of the fine correction plus the coarse read),
-    each level's cells times its bytes per cell."""
-    ncoef = 1 if (dim == 3 and w == 4) else dim
+    each level's cells times its bytes per cell. The coefficients are one
+    array of cell densities on the 3D float32 path's finest level and its
+    first DENSITY_LEVELS coarse levels, else the d face arrays."""
+    def ncoef(i):
+        return 1 if (dim == 3 and w == 4 and i <= DENSITY_LEVELS) else dim
     frac = 1.0 / 2 ** dim
-    gs = sum(c * ((1 + dim + 1) * w + (pre - 1 + post) * (1 + 1 + dim + 1) * w) for c in levels[1:])
-    rs = sum(c * (((2 + (ncoef if i == 0 else dim)) * w) + w * frac) for i, c in enumerate(levels))
+    gs = sum(c * ((1 + ncoef(i) + 1) * w + (pre - 1 + post) * (1 + 1 + ncoef(i) + 1) * w)
+             for i, c in enumerate(levels) if i >= 1)
+    rs = sum(c * (((2 + ncoef(i)) * w) + w * frac) for i, c in enumerate(levels))
     pr = sum(c * (2 * w + w * frac) for c in levels)
     return {"mg_gs_coarse_levels": gs, "mg_restrict": rs, "mg_prolong": pr}
 

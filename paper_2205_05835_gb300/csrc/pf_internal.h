@@ -130,11 +130,20 @@ struct MGLevel {
 // arrays of one context.
 struct SweepTMA;
 
+// Coarse levels whose operator is rediscretised from cell densities (the mean
+// of the 8 children's) instead of face coefficients averaged from the level
+// above (3D float32 path).
+constexpr int kDensityLevels = 1;
+
 template <typename T>
 struct MGHier {
     const float* rho0 = nullptr;   // float32 cell densities of level 0 (3D mixed path), formed
                                    // once per solve; the finest sweep reads them instead of phi
+    float* rhoc[kMaxLevels] = {};  // densities of the tiled levels 1 .. kDensityLevels (mean of the 8
+                                   // children's), from which their face coefficients are
+                                   // formed (3D mixed path; nullptr elsewhere)
     const SweepTMA* tma = nullptr; // level 0 sweeps staged by the TMA (nullptr: cp.async)
+    const SweepTMA* tmac[kMaxLevels] = {};   // the same for the levels l >= 1 with densities
     int nlev;
     int first_coarse;   // levels >= first_coarse are handled by one single-CTA kernel
     int pre, post;

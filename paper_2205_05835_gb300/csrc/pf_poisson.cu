@@ -308,6 +308,37 @@ k_coarsen_beta(MGLevel<T> F, MGLevel<T> C, const T* __restrict__ phi, Phys ph) {
     });
 }
 
+// 3D float32, a tiled coarse level from the cell densities of the level above:
+// the coarse density of a cell is the mean of its 8 children's (stored in
+// rhoc), and the face coefficient is 1 / rho_f of the two coarse densities (a
+// rediscretised coarse operator, which the level's TMA-staged sweep and
+// restriction form from rhoc the way level 0's do from its densities)
+__global__ void __launch_bounds__(kThreads)
+k_beta_rho(MGLevel<float> C, const float* __restrict__ rhof, Dims fg, float* __restrict__ rhoc) {
+    for_cells(C.g, [&](int ci, int cj, int ck, int I) {
+        auto mean8 = [&](int a, int b, int c) {
+            float s = 0.f;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx)
+                        s += __ldg(rhof + ((size_t)(2 * c + dz) * fg.ny + 2 * b + dy) * fg.nx +
+                                   2 * a + dx);
+            return 0.125f * s;
+        };
+        const float rc = mean8(ci, cj, ck);
+        rhoc[I] = rc;
+        const float rx = mean8(wrapi(ci - 1, C.g.nx), cj, ck);
+        const float ry = mean8(ci, wrapi(cj - 1, C.g.ny), ck);
+        const float rz = mean8(ci, cj, wrapi(ck - 1, C.g.nz));
+        C.beta[0][I] = __frcp_rn(0.5f * (rc + rx));
+        C.beta[1][I] = __frcp_rn(0.5f * (rc + ry));
+        C.beta[2][I] = __frcp_rn(0.5f * (rc + rz));
+    });
+}
+
 // float64 face coefficients 1 / rho_f (float64 path)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
@@ -548,9 +579,19 @@ void coarse_smem_attribute() {
 
 template <typename T, int DIM>
 void launch_mg_setup(const Dims&, const Phys& ph, const T* phi, MGHier<T>& H, cudaStream_t s) {
-    for (int l = 0; l + 1 < H.nlev; ++l)
+    for (int l = 0; l + 1 < H.nlev; ++l) {
+        if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+            const float* rf = l == 0 ? H.rho0 : H.rhoc[l];
+            if (rf != nullptr && H.rhoc[l + 1] != nullptr) {
+                k_beta_rho<<<row_grid(H.lev[l + 1].g, kThreads, 1 << 30), kThreads, 0, s>>>(
+                    reinterpret_cast<const MGLevel<float>&>(H.lev[l + 1]), rf, H.lev[l].g,
+                    H.rhoc[l + 1]);
+                continue;
+            }
+        }
         k_coarsen_beta<T, DIM><<<row_grid(H.lev[l + 1].g, kThreads, 1 << 30), kThreads, 0, s>>>(
             H.lev[l], H.lev[l + 1], phi, ph);
+    }
 }
 
 template <typename T, int DIM>
@@ -579,6 +620,12 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
     // finest tiled sweep: the precomputed cell densities when present, else phi
     const float* phi0 = H.rho0 != nullptr ? H.rho0 : reinterpret_cast<const float*>(phi);
     const int rho_ready = H.rho0 != nullptr ? 1 : 0;
+    // coefficient source of a tiled level's sweep: the level's densities (phi
+    // on level 0 without them), else its face arrays
+    auto dens = [&](int l) -> const float* {
+        return l == 0 ? phi0 : (H.rho0 != nullptr ? H.rhoc[l] : nullptr);
+    };
+    auto rho_ready_of = [&](int l) { return l == 0 ? rho_ready : 1; };
     T* fin[kMaxLevels];   // buffer holding each level's result
     for (int l = l0; l < H.nlev; ++l) fin[l] = H.lev[l].x;
     auto gs = [&](const MGLevel<T>& L, int lvl, int color, int zero) {
@@ -600,11 +647,11 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
                     const float* xin = p == 0 ? nullptr : reinterpret_cast<const float*>(cur);
                     float* xout = reinterpret_cast<float*>(p == 0 ? cur : oth);
-                    if (!(l == 0 && launch_sweep_tma(H.tma, reinterpret_cast<const MGLevel<float>&>(L),
+                    if (!(launch_sweep_tma(l == 0 ? H.tma : H.tmac[l],
+                                                     reinterpret_cast<const MGLevel<float>&>(L),
                                                      xin, xout, nullptr, 0, sc, s)))
-                        launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
-                                       l == 0 ? phi0 : nullptr, rho_ready, ph, xin, xout, nullptr, 0,
-                                       sc, s);
+                        launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L), dens(l),
+                                       rho_ready_of(l), ph, xin, xout, nullptr, 0, sc, s);
                     pr->end();
                     if (p > 0) { T* t = cur; cur = oth; oth = t; }
                 }
@@ -624,7 +671,7 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
             if (L.beta[0] != nullptr && restrict3d_ok(L.g)) {
                 launch_restrict3d(reinterpret_cast<const MGLevel<float>&>(L),
                                   reinterpret_cast<const MGLevel<float>&>(H.lev[l + 1]),
-                                  l == 0 ? H.rho0 : nullptr, sc, s);
+                                  l == 0 ? H.rho0 : H.rhoc[l], sc, s);
                 done_r = true;
             }
         }
@@ -679,11 +726,12 @@ T* launch_vcycle(const Phys& ph, const T* phi, MGHier<T>& H, const CGScalars* sc
                     pr->begin(l == 0 ? KC_GS0 : KC_GS);
                     const float* xin = reinterpret_cast<const float*>(cur);
                     float* xout = reinterpret_cast<float*>(oth);
-                    if (!(l == 0 && launch_sweep_tma(H.tma, reinterpret_cast<const MGLevel<float>&>(L),
+                    if (!(launch_sweep_tma(l == 0 ? H.tma : H.tmac[l],
+                                                     reinterpret_cast<const MGLevel<float>&>(L),
                                                      xin, xout, fuse ? dots : nullptr, 1, sc, s)))
-                        launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L),
-                                       l == 0 ? phi0 : nullptr, rho_ready, ph, xin, xout,
-                                       fuse ? dots : nullptr, 1, sc, s);
+                        launch_sweep3d(reinterpret_cast<const MGLevel<float>&>(L), dens(l),
+                                       rho_ready_of(l), ph, xin, xout, fuse ? dots : nullptr, 1,
+                                       sc, s);
                     pr->end();
                     if (fuse && dots_done) *dots_done = true;
                     T* t = cur; cur = oth; oth = t;

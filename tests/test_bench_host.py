@@ -50,8 +50,14 @@ def test_multilevel_classes_in_the_step_roofline(bench):
     assert bench.mg_levels((256, 256, 1), 2) == [256 ** 2, 128 ** 2]
     lv = bench.mg_levels((64, 64, 64), 3)
     cb = bench.coarse_class_bytes(lv, 3, 4)
-    # restriction: finest level x, f, rho (12 B) + 1/8 coarse write, then faces
-    assert cb["mg_restrict"] == lv[0] * 12.5 + lv[1] * 20.5
+    # restriction: x, f, rho (12 B) + 1/8 coarse write on the finest level and
+    # level 1 (densities), x, f and three face arrays below
+    assert cb["mg_restrict"] == lv[0] * 12.5 + lv[1] * 12.5
+    # sweeps of level 1 from its densities: 12 B from zero, 16 B from x_in
+    assert cb["mg_gs_coarse_levels"] == lv[1] * (12 + 16)
+    lv4 = bench.mg_levels((384, 384, 384), 3)
+    cb4 = bench.coarse_class_bytes(lv4, 3, 4)
+    assert cb4["mg_restrict"] == sum(c * (12.5 if i <= 1 else 20.5) for i, c in enumerate(lv4))
     assert cb["mg_prolong"] == sum(c * 8.5 for c in lv)
     prof = {"mg_gs_level0": (10, 2.0), "mg_restrict": (20, 1.0), "mg_prolong": (20, 1.0),
             "mg_gs_coarse_levels": (20, 1.0), "mg_coarse_vcycle": (10, 0.5)}

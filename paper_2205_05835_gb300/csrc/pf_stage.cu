@@ -677,13 +677,15 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_gamma(Dims g, const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
         double gamma_fixed, double gamma_min, double* gamma, RedBuf rb) {
-    double m = 0.0;
+    // the maximum of |u| is exact in the storage precision: float32 values
+    // are compared on the float32 pipe and widened once per thread
+    T m = T(0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.ncell; i += gridDim.x * blockDim.x) {
-        m = fmax(m, fabs(double(u0[i])));
-        m = fmax(m, fabs(double(u1[i])));
-        if (DIM == 3) m = fmax(m, fabs(double(u2[i])));
+        m = max(m, abs(u0[i]));
+        m = max(m, abs(u1[i]));
+        if (DIM == 3) m = max(m, abs(u2[i]));
     }
-    double v[1] = {m}, tot[1];
+    double v[1] = {double(m)}, tot[1];
     const int mode[1] = {1};
     if (grid_reduce<1>(v, mode, rb, tot) && threadIdx.x == 0)
         *gamma = gamma_fixed > 0.0 ? gamma_fixed : fmax(gamma_min, tot[0]);

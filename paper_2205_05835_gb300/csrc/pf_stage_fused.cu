@@ -35,14 +35,18 @@ constexpr int PL = HX * HY;                   // 480 floats per plane
 constexpr int CPR = HX / 4, NCH = CPR * HY;   // 16-byte chunks per row / plane
 constexpr int RP = 5, RU = 4, RD = 3;         // ring planes: phi, each u, each derived field
 constexpr int RQ = 4;                         // ring planes of the ACDI psi
-constexpr int NR = (TX + 2) * (TY + 2);       // derived-field cells (tile + one-cell ring): 340
+constexpr int RXC = TX + 2;                   // derived-field row (tile + one-cell ring): 34
+constexpr int NR = RXC * (TY + 2);            // derived-field cells: 340
 constexpr int NR2 = (TX + 4) * (TY + 4);      // psi cells (tile + two-cell ring): 432
 
+// the normals and mu are stored on the tile plus a one-cell ring only (34 x
+// 10), which keeps the CTA within a quarter of the SM's shared memory (four
+// resident CTAs); phi, u and psi keep the staged plane's layout
 struct Smem {
     float phi[RP][PL];
     float u[3][RU][PL];
-    float n[3][RD][PL];
-    float mu[RD][PL];
+    float n[3][RD][NR];
+    float mu[RD][NR];
     float psi[RQ][PL];
 };
 
@@ -63,7 +67,7 @@ __device__ __forceinline__ void cp16(float* dst, const float* src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
+__global__ void __launch_bounds__(NTH, 4) k_stage3d_fused(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     const Dims& g = A.g;
@@ -162,15 +166,17 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
             const float* Q1 = S.psi[sq(k + 1)];
             float* Q2 = S.psi[sq(k + 2)];
             for (int c = tid; c < (acdi ? NR2 : NR); c += NTH) {
-                int o;
+                int o, oc;   // staged-plane and derived-field index of the cell
                 if (acdi) {
                     const int ry = c / (TX + 4), rx = c - ry * (TX + 4);
                     o = (ry + OY - 2) * HX + rx + OX - 2;
                     Q2[o] = acdi_psi(P2[o], eps);
                     if (ry < 1 || ry > TY + 2 || rx < 1 || rx > TX + 2) continue;   // outer ring
+                    oc = (ry - 1) * RXC + rx - 1;
                 } else {
-                    const int ry = c / (TX + 2), rx = c - ry * (TX + 2);
+                    const int ry = c / RXC, rx = c - ry * RXC;
                     o = (ry + OY - 1) * HX + rx + OX - 1;
+                    oc = c;
                 }
                 const float pc = P1[o];
                 const float xm = P1[o - 1], xp = P1[o + 1], ym = P1[o - HX], yp = P1[o + HX];
@@ -188,14 +194,14 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
                 float s = g0 * g0 + g1 * g1;
                 s += g2 * g2;
                 const float den = sqrtf(s) + A.dn;
-                N0[o] = divq(g0, den);
-                N1[o] = divq(g1, den);
-                N2[o] = divq(g2, den);
+                N0[oc] = divq(g0, den);
+                N1[oc] = divq(g1, den);
+                N2[oc] = divq(g2, den);
                 float lap = 0.f;
                 lap = lap + (xp - 2.f * pc + xm) * inv_h2;
                 lap = lap + (yp - 2.f * pc + ym) * inv_h2;
                 lap = lap + (zp - 2.f * pc + zm) * inv_h2;
-                MU[o] = dwell32(pc, A.c_dw_hi, A.c_dw_lo) - A.c_lap * lap;
+                MU[oc] = dwell32(pc, A.c_dw_hi, A.c_dw_lo) - A.c_lap * lap;
             }
         }
         __syncthreads();   // derived fields of plane k + 1 visible
@@ -220,6 +226,11 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
         auto at = [&](const float* const* pl, int dx, int dy, int dz) {
             return pl[1 + dz][cs + dx + dy * HX];
         };
+        // the same for the derived fields (n, mu) on the tile plus ring
+        const int csd = (ty + 1) * RXC + tx + 1;
+        auto atd = [&](const float* const* pl, int dx, int dy, int dz) {
+            return pl[1 + dz][csd + dx + dy * RXC];
+        };
         // offset vectors of +/- e_d
         auto ax = [](int d, int o, int (&v)[3]) { v[0] = v[1] = v[2] = 0; v[d] = o; };
         const float pc = Pp[1][cs];
@@ -235,13 +246,13 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
                 ax(d, 1, p);
                 const float pm = at(Pp, m[0], m[1], m[2]);
                 const float pf = 0.5f * (pc + pm);
-                const float nf = 0.5f * (Np[d][1][cs] + at(Np[d], m[0], m[1], m[2]));
+                const float nf = 0.5f * (Np[d][1][csd] + atd(Np[d], m[0], m[1], m[2]));
                 const float shlo = acdi ? acdi_sharp(0.5f * (psc + at(Qp, m[0], m[1], m[2])), eps)
                                         : pf * (1.f - pf);
                 const float Flo = Up[d][1][cs] * pf - gam * (eps * ((pc - pm) * inv_h) - shlo * nf);
                 const float pp = at(Pp, p[0], p[1], p[2]);
                 const float pf2 = 0.5f * (pp + pc);
-                const float nf2 = 0.5f * (at(Np[d], p[0], p[1], p[2]) + Np[d][1][cs]);
+                const float nf2 = 0.5f * (atd(Np[d], p[0], p[1], p[2]) + Np[d][1][csd]);
                 const float shhi = acdi ? acdi_sharp(0.5f * (at(Qp, p[0], p[1], p[2]) + psc), eps)
                                         : pf2 * (1.f - pf2);
                 const float Fhi = at(Up[d], p[0], p[1], p[2]) * pf2 -
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(NTH, 3) k_stage3d_fused(FusedArgs A) {
             }
             // energy-based surface tension force at the face (Eq. eb_st)
             const float dphi = (pc - pm) * inv_h;
-            const float F = 0.5f * (Mp[1][cs] + at(Mp, m[0], m[1], m[2])) * dphi;
+            const float F = 0.5f * (Mp[1][csd] + atd(Mp, m[0], m[1], m[2])) * dphi;
             const float beta = divq(1.f, 0.5f * (rho_of_p(pc, pcs) + rho_of_p(pm, pcs)));
             ku[d] = -adv + beta * visc + beta * F;
         }
@@ -392,7 +403,7 @@ void launch_stage_fused(const Dims& g, const Phys& ph, const StageIO<float>& io,
     a.c_lap = float(sh * ph.eps);
     const long long cols = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int zc = 64;
-    while (zc > 4 && cols * ((g.nz + zc - 1) / zc) < 3 * 152) zc >>= 1;
+    while (zc > 4 && cols * ((g.nz + zc - 1) / zc) < 4 * 152) zc >>= 1;
     a.zc = zc;
     fused_attributes();
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + zc - 1) / zc);

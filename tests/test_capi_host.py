@@ -244,3 +244,33 @@ def test_mg_coarse_cells_validation_and_autotune_keys(pf):
     assert {"mg_coarse_cells": 16384, "mg_pre": 1, "mg_post": 1} in autotune.CANDIDATES
     tuned = autotune.apply(a, {"choice": autotune.CANDIDATES[2]})
     assert tuned["mg_coarse_cells"] == 16384 and tuned["sigma"] == a["sigma"]
+
+
+def test_autotune_keeps_defaults_within_the_margin(pf, monkeypatch):
+    """Host logic of tune() with the timing replaced: a candidate must beat the
+    library's defaults by more than MARGIN to be chosen, in the multigrid stage
+    and in the 3D mixed tile stage; a clearly faster one is chosen."""
+    from paper_2205_05835_gb300 import autotune
+
+    def run(times, p):
+        def fake(pf_, p_, cand, steps, warm):
+            key = tuple(sorted(cand.items()))
+            return times.get(key, 1.0)
+        monkeypatch.setattr(autotune, "_time_candidate", fake)
+        autotune._cache.clear()
+        return autotune.tune(p, candidates=cands)["choice"]
+
+    d = autotune.DEFAULT_SHAPE
+    other = {"mg_coarse_cells": 1024, "mg_pre": 2, "mg_post": 2}
+    cands = (d, other)
+    k = lambda c: tuple(sorted(c.items()))  # noqa: E731
+    p2 = {"dim": 2, "n": (64, 64, 1), "precision": "mixed", "rho_in": 10.0, "rho_out": 1.0}
+    # 0.5 % faster: keep the defaults; 3 % faster: take the candidate
+    assert run({k(d): 1.0, k(other): 0.995}, p2) == d
+    assert run({k(d): 1.0, k(other): 0.97}, p2) == other
+    # 3D mixed: tile shapes are tried after the shape, with the same margin
+    p3 = dict(p2, dim=3, n=(64, 64, 64))
+    t2 = dict(d, sweep_tile=2)
+    t3 = dict(d, sweep_tile=3)
+    assert run({k(d): 1.0, k(other): 1.2, k(t2): 0.995, k(t3): 1.1}, p3) == d
+    assert run({k(d): 1.0, k(other): 1.2, k(t2): 0.98, k(t3): 0.95}, p3) == t3

@@ -184,7 +184,6 @@ bool sweep_tma_ok(const Dims& g);
 SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, const float* xa,
                            const float* xb, int tile);
 void sweep_tma_destroy(SweepTMA* t);
-int sweep_tma_tile(const SweepTMA* t);   // shape code in use, 0 .. 4 (-1: no object)
 void sweep_tma_prepare();
 bool launch_sweep_tma(const SweepTMA* t, const MGLevel<float>& L, const float* xin, float* xout,
                       const SweepDots* dots, int first_color, const CGScalars* sc,

@@ -42,10 +42,6 @@ namespace {
 
 using namespace tma;
 
-#ifndef PF_TMA_BOXES
-#define PF_TMA_BOXES 1
-#endif
-
 constexpr int TX = 32, OX = 4;                // tile width, staged columns left of it
 constexpr int HX = TX + 2 * OX;               // 40 columns of a staged plane
 constexpr int RXS = TX + 2;                   // one-cell ring around the tile, x
@@ -168,7 +164,7 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
         // full barriers: one arrival with the expected bytes of the tensor
         // copies (interior tiles), or one cp.async-tracking arrival per
         // producer lane (tiles across a seam)
-        const unsigned nfull = (PF_TMA_BOXES && interior) ? 1u : (unsigned)NC;
+        const unsigned nfull = interior ? 1u : (unsigned)NC;
         for (int s = 0; s < RING; ++s) {
             mbar_init(&S.bar_r[s], nfull);
             mbar_init(&S.bar_xf[s], nfull);
@@ -181,7 +177,7 @@ k_sweep3d_tma(const __grid_constant__ CUtensorMap tm_rho, const __grid_constant_
     }
     __syncthreads();
 
-    const bool tma = PF_TMA_BOXES && interior;
+    const bool tma = interior;
     if (tid >= NC) {
         // ---------------- producer warp (tiles away from the seams) ----------------
         for (int q = 0; q <= (tma ? QMAX : -1); ++q) {
@@ -444,7 +440,6 @@ struct SweepTMA {
     int ty;               // tile height, 8 or 16
     int cpt_zero;         // cells per thread and plane of zero-start sweeps, 1 or 2
     int cpt_full;         // the same for sweeps from a given x_in
-    int tile;             // the pf_params.sweep_tile code
     Dims g;
     CUtensorMap rho, f, xa, xb;
     const float* rho_p;
@@ -476,7 +471,6 @@ SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, cons
     // rows within the grid (else 32 x 8).
     const bool tall = (tile == 2 || tile == 3) && g.ny >= TileCfg<16, 1>::HY;
     t->ty = tall ? 16 : 8;
-    t->tile = tile;
     t->cpt_zero = (tile == 3 || tile == 4) ? 1 : 2;
     t->cpt_full = (tile == 1 || tile == 2) ? 2 : 1;
     t->stall = std::getenv("PF_TEST_SWEEP_STALL") != nullptr ? 1 : 0;
@@ -491,7 +485,6 @@ SweepTMA* sweep_tma_create(const Dims& g, const float* rho, const float* f, cons
 
 void sweep_tma_destroy(SweepTMA* t) { delete t; }
 
-int sweep_tma_tile(const SweepTMA* t) { return t ? t->tile : -1; }
 
 void sweep_tma_prepare() {
     tma_attributes<true, 8, 2>();
